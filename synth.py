@@ -1,0 +1,93 @@
+"""Seeded synthetic inputs shared by the tests and the bench.
+
+This module holds no FFT arithmetic: it only draws random numbers and
+evaluates closed-form fields on the grid.  Both the CUDA path and the FP64
+oracle consume what it returns, so they see bit-identical inputs.
+
+Every generator draws from ``numpy.random.default_rng(seed)`` (PCG64) in FP64;
+FP32 runs round the FP64 field once.  Grid coordinates follow Sec. 2 of arXiv
+2202.12756: the field is periodic on (2 pi)^3 with N points per axis, so
+x_j = 2 pi j / N, and the last (fastest) axis is z.
+"""
+import numpy as np
+
+
+def uniform_field(shape, seed):
+    """iid uniform[-1, 1) real field in FP64."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-1.0, 1.0, size=tuple(shape))
+
+
+def eq5_field(n0, n1, n2):
+    """Eq. 5 test field: 8 sin x sin 2y sin 3z + 8 sin 4x sin 5y sin 6z."""
+    x = 2.0 * np.pi * np.arange(n0) / n0
+    y = 2.0 * np.pi * np.arange(n1) / n1
+    z = 2.0 * np.pi * np.arange(n2) / n2
+    t1 = np.sin(x)[:, None, None] * np.sin(2 * y)[None, :, None] * np.sin(3 * z)[None, None, :]
+    t2 = np.sin(4 * x)[:, None, None] * np.sin(5 * y)[None, :, None] * np.sin(6 * z)[None, None, :]
+    return 8.0 * t1 + 8.0 * t2
+
+
+def plane_wave_vectors(seed, count=8, kmax=256):
+    """`count` random integer wave vectors with |k_i| < kmax (signed)."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(-(kmax - 1), kmax, size=(count, 3))
+
+
+def _cos_phase_1d(k, n):
+    # exp(2 pi i k j / n) for j < n, with k j reduced mod n exactly
+    p = (int(k) * np.arange(n, dtype=np.int64)) % n
+    return np.exp(2j * np.pi * p / n)
+
+
+def plane_waves(shape, kvecs):
+    """sum over k of cos(2 pi (k0 j0/N0 + k1 j1/N1 + k2 j2/N2)), in FP64."""
+    n0, n1, n2 = shape
+    out = np.zeros(shape, dtype=np.float64)
+    for k0, k1, k2 in kvecs:
+        e0 = _cos_phase_1d(k0, n0)
+        e1 = _cos_phase_1d(k1, n1)
+        e2 = _cos_phase_1d(k2, n2)
+        # cos(a + b + c) = Re(e^{ia} e^{ib} e^{ic}); one plane of axis 0 at a time
+        e12 = e1[:, None] * e2[None, :]
+        for j0 in range(n0):
+            out[j0] += (e0[j0] * e12).real
+    return out
+
+
+def signed_wavenumbers(n):
+    """k = idx for idx <= n/2, idx - n above, as integers (FFTW order)."""
+    k = np.arange(n, dtype=np.int64)
+    return np.where(k <= n // 2, k, k - n)
+
+
+def turbulence_spectrum(n0, n1, n2, seed, kmin=1.0, kmax=None, slope=-11.0 / 6.0):
+    """Half spectrum [n0][n1][n2//2+1] with random phases and |k|^slope amplitude.
+
+    Amplitude |k|^(-11/6) on kmin <= |k| <= kmax (kmax defaults to N/2 of the
+    smallest axis), zero elsewhere; phases iid uniform[0, 2 pi).  Signed
+    wavenumbers on axes 0 and 1, k2 = 0..n2/2 on the halved axis.
+    """
+    if kmax is None:
+        kmax = min(n0, n1, n2) // 2
+    rng = np.random.default_rng(seed)
+    m1 = n2 // 2 + 1
+    k0 = signed_wavenumbers(n0).astype(np.float64)
+    k1 = signed_wavenumbers(n1).astype(np.float64)
+    k2 = np.arange(m1, dtype=np.float64)
+    out = np.empty((n0, n1, m1), dtype=np.complex128)
+    k12sq = k1[:, None] ** 2 + k2[None, :] ** 2
+    for i in range(n0):
+        kk = np.sqrt(k0[i] ** 2 + k12sq)
+        amp = np.where((kk >= kmin) & (kk <= kmax), np.power(np.maximum(kk, 1e-300), slope), 0.0)
+        phase = rng.uniform(0.0, 2.0 * np.pi, size=(n1, m1))
+        out[i] = amp * np.exp(1j * phase)
+    return out
+
+
+def random_half_spectrum(shape, seed):
+    """iid complex normal half spectrum (not Hermitian-consistent on the edge planes)."""
+    n0, n1, n2 = shape
+    rng = np.random.default_rng(seed)
+    m1 = n2 // 2 + 1
+    return rng.standard_normal((n0, n1, m1)) + 1j * rng.standard_normal((n0, n1, m1))
