@@ -1,0 +1,377 @@
+"""Benchmark: 3D R2C + C2R FFT pair on one GB300 (replicas across GPUs).
+
+One step = one forward R2C + one normalised inverse C2R of a 1024^3 real
+grid, in place in the padded layout, FP32 storage and arithmetic (twiddles
+generated in FP64).  The same pair in FP64 is timed too and reported under
+"fp64".  Input: the synthetic turbulence-like field (random-phase Fourier
+modes, amplitude |k|^(-11/6) for 1 <= |k| <= 512, seed 2) taken to real space
+by the library's own FP64 inverse, normalised to unit RMS and rounded once to
+FP32.  The arrays (4.3 GB FP32, 8.6 GB FP64) are far larger than the 129 MB
+L2, so no L2 flush is needed between steps.
+
+metric: GFLOP/s with 2.5 N^3 log2(N^3) flops per real transform (5 per pair
+element-log), i.e. 5 N^3 log2(N^3) per pair; also HBM GB/s of the three
+read+write passes per transform.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n N]
+Under torchrun each rank times its own replica; rank 0 prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "R2C+C2R 3D FFT GFLOP/s & HBM GB/s, FP32 vs FP64 at 1024³, 1×GB300"
+UNIT = "GFLOP/s"
+
+
+def pair_flops(n0, n1, n2):
+    """2.5 N log2 N per real transform of N points, two transforms per pair."""
+    n = n0 * n1 * n2
+    return 2 * 2.5 * n * math.log2(n)
+
+
+def pass_bytes(n0, n1, n2, rsize):
+    """HBM bytes of the 3 read+write passes of one transform."""
+    c = n0 * n1 * (n2 // 2 + 1) * 2 * rsize
+    r = n0 * n1 * n2 * rsize
+    return (c + r) + 2 * c + 2 * c
+
+
+def kernel_sources_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2202_12756_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d.get("hbm_gbs"), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+def ncu_traffic(workload):
+    """Per-launch DRAM bytes of each pass from the committed ncu summary, or
+    None when the kernels changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_hash") != kernel_sources_hash():
+        return None
+    return d.get("workloads", {}).get(workload)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=5)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def max_over_ranks(x, pg, device=None):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_field(n, dev):
+    """Turbulence-like field of the headline workload, FP64 on the device,
+    padded in-place layout, unit RMS."""
+    import torch
+
+    import synth
+    import paper_2202_12756_gb300 as fft3d
+    plan64 = fft3d.get_plan((n, n, n), torch.float64, dev)
+    buf = plan64.empty_padded()
+    spec = buf.view(torch.complex128)
+    spec.copy_(synth.turbulence_spectrum_device(n, n, n, seed=2, device=dev))
+    plan64.c2r_(buf)
+    view = buf[..., :n]
+    rms = torch.sqrt(torch.mean(view * view))
+    view.div_(rms)
+    torch.cuda.synchronize(dev)
+    return plan64, buf
+
+
+def time_pairs(plan, buf, steps, warmup, dev, pg, profile=False):
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(warmup):
+        plan.r2c_(buf)
+        plan.c2r_(buf)
+    if pg is not None:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    plan.profile_read()  # clear
+    plan.set_profiling(profile)
+    l0 = plan.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        plan.r2c_(buf)
+        plan.c2r_(buf)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if pg is not None:
+        pg.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = plan.launch_count() - l0
+    stats = plan.profile_read() if profile else []
+    plan.set_profiling(False)
+    return ms, launches, stats
+
+
+def roofline_from(stats, peak_gbs, traffic):
+    if not stats:
+        return None
+    top = max(stats, key=lambda s: s["total_ms"])
+    avg_ms = top["total_ms"] / top["launches"]
+    achieved = top["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": top["name"], "achieved": round(achieved, 1), "peak": peak_gbs,
+            "unit": "GB/s", "frac": round(achieved / peak_gbs, 4),
+            "traffic": (traffic or {}).get(top["name"]),
+            "avg_launch_ms": round(avg_ms, 4),
+            "per_pass_ms": {s["name"]: round(s["total_ms"] / s["launches"], 4) for s in stats}}
+
+
+def cpu_baseline(budget_s=12.0, n=256):
+    """FP64 oracle pairs at n^3 on the host cores for about budget_s seconds."""
+    import oracle
+    import synth
+    f = synth.uniform_field((n, n, n), 0)
+    oracle.irfft3(oracle.rfft3(f), f.shape)  # warm the library
+    t0 = time.perf_counter()
+    pairs = 0
+    while True:
+        oracle.irfft3(oracle.rfft3(f), f.shape)
+        pairs += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(pair_flops(n, n, n) * pairs / dt / 1e9, 3), "unit": UNIT,
+            "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{pairs} FP64 R2C+C2R pairs of a {n}^3 uniform field ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    n = args.ref_n
+    f = synth.uniform_field((n, n, n), 0)
+    for _ in range(args.warmup):
+        oracle.irfft3(oracle.rfft3(f), f.shape)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.irfft3(oracle.rfft3(f), f.shape)
+    dt = time.perf_counter() - t0
+    val = pair_flops(n, n, n) * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(val, 3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.n}^3 R2C+C2R pair; reference arm: FP64 CPU oracle on a "
+                                   f"{n}^3 sample per step", "grid": [n, n, n]},
+            "cpu_baseline": {"value": round(val, 3), "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": f"one {n}^3 FP64 pair per step"},
+            "e2e": {"value": round(val, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local, pg = dist_setup(args)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    import paper_2202_12756_gb300 as fft3d
+    fft3d.load_library()
+    n = args.n
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"]
+
+    plan64, buf64 = make_field(n, dev)
+    plan32 = fft3d.get_plan((n, n, n), torch.float32, dev)
+    buf32 = plan32.empty_padded()
+    buf32.copy_(buf64)
+
+    # ---- FP32 headline: device-resident inputs
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms32, launches32, stats32 = time_pairs(plan32, buf32, args.steps, args.warmup, dev, pg, profile=True)
+    clk = clocks.stop()
+    ms32 = max_over_ranks(ms32, pg, dev)
+    t_step = ms32 / args.steps
+    flops = pair_flops(n, n, n)
+    bytes_pair = 2 * pass_bytes(n, n, n, 4)
+    value = flops * world / (t_step * 1e-3) / 1e9
+
+    # ---- FP64 pair (same field)
+    ms64, launches64, stats64 = time_pairs(plan64, buf64, max(2, args.steps // 4), args.warmup, dev, pg,
+                                           profile=True)
+    ms64 = max_over_ranks(ms64, pg, dev)
+    t64 = ms64 / max(2, args.steps // 4)
+
+    # ---- end to end through the public API: pinned host in, pinned host out
+    host_in = torch.empty((n, n, n), dtype=torch.float32, pin_memory=True)
+    host_in.copy_(buf32[..., :n])
+    host_out = torch.empty_like(host_in, pin_memory=True)
+    stream = torch.cuda.current_stream(dev)
+    e2e_steps = max(2, args.steps // 4)
+    for _ in range(2):
+        buf32[..., :n].copy_(host_in, non_blocking=True)
+        plan32.r2c_(buf32)
+        plan32.c2r_(buf32)
+        host_out.copy_(buf32[..., :n], non_blocking=True)
+    torch.cuda.synchronize(dev)
+    if pg is not None:
+        pg.barrier()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(e2e_steps):
+        buf32[..., :n].copy_(host_in, non_blocking=True)
+        plan32.r2c_(buf32)
+        plan32.c2r_(buf32)
+        host_out.copy_(buf32[..., :n], non_blocking=True)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_e2e = max_over_ranks(a.elapsed_time(b), pg, dev) / e2e_steps
+    e2e_val = flops * world / (ms_e2e * 1e-3) / 1e9
+    io_bytes = n * n * n * 4
+
+    traffic = ncu_traffic(f"{n}^3 f32")
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{n}^3 real grid, R2C+C2R pair in place (padded rows), FP32, "
+                               f"turbulence-like field (|k|^-11/6, seed 2)",
+                   "grid": [n, n, n], "layout": "in-place padded", "parallelism": f"replicas x{world}",
+                   "l2": "inputs (4.3 GB) larger than L2, no flush"},
+        "hbm_gbs": round(bytes_pair / (t_step * 1e-3) / 1e9, 1),
+        "hbm_frac_of_peak": round(bytes_pair / (t_step * 1e-3) / 1e9 / peak, 4),
+        "gflops_paper_convention": round(2 * value, 1),
+        "roofline": roofline_from(stats32, peak, traffic),
+        "fp64": {"ms_per_step": round(t64, 3),
+                 "gflops": round(flops * world / (t64 * 1e-3) / 1e9, 1),
+                 "hbm_gbs": round(2 * pass_bytes(n, n, n, 8) / (t64 * 1e-3) / 1e9, 1),
+                 "per_pass_ms": {s["name"]: round(s["total_ms"] / s["launches"], 3) for s in stats64},
+                 "fp32_speedup": round(t64 / t_step, 2)},
+        "e2e": {"value": round(e2e_val, 1), "unit": UNIT, "ms_per_step": round(ms_e2e, 3),
+                "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
+        "gpu_launches": int(launches32),
+        "clocks": clk,
+        "peak_source": peaks["src"],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--ref-n", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,158 @@
+/*
+ * fft3d -- single-GPU 3D real FFT for GB300 (sm_103a).
+ *
+ * C ABI.  Plain pointers and sizes only; no C++ or framework types cross it.
+ * Every function returns a status code (enum fft3d_status); none throws.
+ *
+ * Operation (arXiv 2202.12756, Sec. 2):
+ *   forward  F[k0][k1][k2] = sum_j f[j0][j1][j2] exp(-2 pi i (j0 k0/N0 + j1 k1/N1 + j2 k2/N2))
+ *            (Eq. 1, unnormalised), stored for k2 = 0 .. N2/2 only (Eqs. 3-4:
+ *            the spectrum of a real field is Hermitian, so half is kept).
+ *   inverse  f[j] = (1/(N0 N1 N2)) sum_k Ft[k] exp(+2 pi i ...)  (Eq. 2 over the
+ *            Hermitian extension Ft of the stored half, followed by the
+ *            normalisation step of Sec. 4).
+ * The paper's slab pipeline (Sec. 3: plane FFTs, transposes, all-to-all,
+ * line FFTs along the slowest axis) runs here as three passes over HBM on one
+ * GPU: contiguous-axis R2C/C2R lines, then strided C2C columns along axis 1,
+ * then strided C2C columns along axis 0 (reversed for the inverse).
+ *
+ * Arrays are C order, axis 2 fastest.  N2 is the halved axis.
+ *   real array     [N0][N1][N2]       dense (out-of-place), or
+ *                  [N0][N1][2(N2/2+1)] padded rows (in-place; pad values are
+ *                  neither read nor preserved);
+ *   complex array  [N0][N1][N2/2+1]   interleaved (re, im) pairs of the dtype.
+ * In-place means in == out (the padded layout); any other overlap between
+ * the input and output ranges is FFT3D_ERR_LAYOUT.
+ *
+ * Supported lengths: N0, N1 in {2^k : 0 <= k <= 11} U {3 * 2^k : 0 <= k <= 9};
+ * N2 even with N2/2 in {2^k : 0 <= k <= 10} U {3 * 2^k : 0 <= k <= 8}
+ * (so every axis is at most 2048).  Anything else is FFT3D_ERR_SIZE.
+ *
+ * Devices and streams: a plan belongs to the device that was current when it
+ * was created; every exec call must run with that device current
+ * (FFT3D_ERR_DEVICE otherwise).  `stream` is a cudaStream_t (NULL = legacy
+ * default stream).  Execution is asynchronous with respect to the host; the
+ * caller owns all data buffers and keeps them alive until the stream has
+ * finished.  A plan may be used by one stream at a time (its scratch is
+ * shared between calls); distinct plans are independent.
+ *
+ * Pointers must be device pointers aligned to one complex element
+ * (8 bytes for FFT3D_F32, 16 bytes for FFT3D_F64), else FFT3D_ERR_ALIGN.
+ */
+#ifndef FFT3D_H
+#define FFT3D_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fft3d_plan_s *fft3d_plan;
+
+enum fft3d_dtype {
+    FFT3D_F32 = 0, /* float storage and arithmetic, twiddles generated in FP64 */
+    FFT3D_F64 = 1  /* double storage and arithmetic */
+};
+
+enum fft3d_status {
+    FFT3D_OK = 0,
+    FFT3D_ERR_SIZE = 1,   /* unsupported N0, N1 or N2 */
+    FFT3D_ERR_DTYPE = 2,  /* dtype not in enum fft3d_dtype */
+    FFT3D_ERR_NULL = 3,   /* a required pointer (plan, in, out, result) is NULL */
+    FFT3D_ERR_ALIGN = 4,  /* a data pointer is not aligned to one complex element */
+    FFT3D_ERR_ALLOC = 5,  /* device or host allocation failed */
+    FFT3D_ERR_CUDA = 6,   /* a CUDA call or kernel launch failed; see fft3d_plan_last_error */
+    FFT3D_ERR_LAYOUT = 7, /* input and output overlap without being identical */
+    FFT3D_ERR_DEVICE = 8, /* current device differs from the plan's device */
+    FFT3D_ERR_ARG = 9     /* any other invalid argument */
+};
+
+/*
+ * Create a plan for an N0 x N1 x N2 real transform of the given dtype on the
+ * current device.  Allocates the plan (host) and, on the device, its FP64-
+ * generated twiddle tables (O(N0 + N1 + N2) entries) and an N0*N1-element
+ * complex scratch plane used only by out-of-place fft3d_exec_c2r /
+ * fft3d_exec_r2c_adjoint.  Synchronises the device once (table generation).
+ * On success *plan is set and FFT3D_OK returned; on failure *plan is NULL.
+ */
+int fft3d_plan_create(fft3d_plan *plan, int64_t n0, int64_t n1, int64_t n2, int dtype);
+
+/* Release the plan and its device memory.  NULL is accepted (no-op).
+ * The caller must make sure no stream still runs work of this plan. */
+int fft3d_plan_destroy(fft3d_plan plan);
+
+/*
+ * Forward R2C, Eq. 1 (unnormalised, sign -).
+ *   in_real:  real array (dense [N0][N1][N2], or padded when in_real == out_cplx)
+ *   out_cplx: complex array [N0][N1][N2/2+1]
+ * Out-of-place calls never write in_real.
+ */
+int fft3d_exec_r2c(fft3d_plan plan, const void *in_real, void *out_cplx, void *stream);
+
+/*
+ * Inverse C2R, Eq. 2 (sign +) followed by the 1/(N0 N1 N2) normalisation.
+ *   in_cplx:  complex array [N0][N1][N2/2+1]
+ *   out_real: real array (dense [N0][N1][N2], or padded when in_cplx == out_real)
+ * Input that is not Hermitian-consistent is accepted: the inverse C2C along
+ * axes 0 and 1 runs as is, and along axis 2 only the real parts of the
+ * k2 = 0 and k2 = N2/2 entries are used.
+ * Out-of-place calls never write in_cplx (the plan's scratch plane holds the
+ * k2 = N2/2 column, which does not fit in the dense real output).
+ */
+int fft3d_exec_c2r(fft3d_plan plan, const void *in_cplx, void *out_real, void *stream);
+
+/*
+ * Adjoint (vector-Jacobian product) of fft3d_exec_r2c with respect to its
+ * real input: for a cotangent G on the half spectrum (G = dL/dRe F + i dL/dIm F)
+ *   out[j] = Re sum_{k in half spectrum} G[k] exp(+2 pi i k.j/N),
+ * computed as the C2R pipeline with the k2 = 0 and k2 = N2/2 planes weighted
+ * by 2, an overall factor 1/2 and no 1/N^3.  Same layouts and aliasing rules
+ * as fft3d_exec_c2r.  The paper has no adjoint; it follows from Eq. 1.
+ */
+int fft3d_exec_r2c_adjoint(fft3d_plan plan, const void *in_cplx, void *out_real, void *stream);
+
+/*
+ * Adjoint of fft3d_exec_c2r with respect to its complex input: for a real
+ * cotangent g,
+ *   out[k] = (c(k2) / (N0 N1 N2)) sum_j g[j] exp(-2 pi i k.j/N),
+ * c = 1 on the k2 = 0 and k2 = N2/2 planes, 2 elsewhere; computed as the R2C
+ * pipeline with those weights applied in its first pass.  Same layouts and
+ * aliasing rules as fft3d_exec_r2c.  Follows from Eq. 2 and the normalisation.
+ */
+int fft3d_exec_c2r_adjoint(fft3d_plan plan, const void *in_real, void *out_cplx, void *stream);
+
+/* Static text for a status code ("unknown status" for anything else). */
+const char *fft3d_strerror(int status);
+
+/* Text of the last error recorded on this plan ("" if none). */
+const char *fft3d_plan_last_error(fft3d_plan plan);
+
+/* 1 if n is a supported length for `axis` (0, 1 or 2), else 0. */
+int fft3d_supported_length(int64_t n, int axis);
+
+/*
+ * Per-kernel timing of the plan's launches (diagnostics).  While enabled,
+ * each kernel launch is bracketed by CUDA events on the launch stream.
+ * fft3d_plan_profile_read synchronises on the recorded events, writes up to
+ * `max` entries (one per pass kind that ran) into `stats`, sets *count, and
+ * clears the accumulated data.  Enabling costs two event records per launch.
+ */
+typedef struct fft3d_kernel_stat {
+    char name[32];            /* pass kind, e.g. "r2c.z", "c2r.x" */
+    int64_t launches;         /* launches timed */
+    double total_ms;          /* summed event-to-event time */
+    double bytes_per_launch;  /* algorithmic HBM bytes one launch must move */
+} fft3d_kernel_stat;
+
+int fft3d_plan_set_profiling(fft3d_plan plan, int enable);
+int fft3d_plan_profile_read(fft3d_plan plan, fft3d_kernel_stat *stats, int max, int *count);
+
+/* Kernel launches issued through this plan since creation. */
+int fft3d_plan_launch_count(fft3d_plan plan, int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFT3D_H */

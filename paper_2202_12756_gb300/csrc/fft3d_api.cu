@@ -1,0 +1,475 @@
+// C-ABI implementation: plans, argument checks, pass sequencing, profiling.
+//
+// Forward (exec_r2c):  z-pass R2C lines -> y-pass C2C columns -> x-pass C2C
+// columns, all on the caller's stream; the y- and x-passes run in place on
+// the output.  This is the single-GPU form of the slab algorithm of Sec. 3 of
+// arXiv 2202.12756: the batched plane FFT (Step 1) is the z- and y-passes, and
+// the transposes, all-to-all and strided line FFT (Steps 2-5) collapse into
+// the x-pass, which reads and writes tiles of adjacent columns directly.
+// Inverse (exec_c2r): the same passes in reverse order ("the above steps in a
+// reverse order", Sec. 3) with the 1/N^3 normalisation fused into the last.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fft3d.h"
+#include "launchers.h"
+
+using namespace fft3d;
+
+namespace {
+
+enum PassKind { K_R2C_Z = 0, K_R2C_Y, K_R2C_X, K_C2R_X, K_C2R_Y, K_C2R_Z, K_COUNT };
+const char *const kPassName[K_COUNT] = {"r2c.z", "r2c.y", "r2c.x", "c2r.x", "c2r.y", "c2r.z"};
+
+// half length M = N2 / 2 of the contiguous axis: 2^k <= 1024 or 3 * 2^k <= 768
+bool z_half_supported(int64_t m)
+{
+    if (m < 1) return false;
+    if (m <= 1024 && is_pow2((int)m)) return true;
+    return m % 3 == 0 && m <= 768 && is_pow2((int)(m / 3));
+}
+
+bool col_supported(int64_t n) { return n >= 1 && n <= 2048 && line_supported((int)n); }
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct fft3d_plan_s {
+    int64_t n0, n1, n2, m, m1;
+    int dtype;
+    int device;
+    size_t rsize, csize;  // bytes of one real / one complex element
+    void *tw;             // device: all twiddle tables
+    const void *tw0, *tw1, *twz, *rot;
+    void *nyq;            // device: [n0][n1] complex scratch (k2 = M column)
+    PassGeom g0, g1, gz;
+    char err[512];
+    int profiling;
+    struct Rec {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    double acc_ms[K_COUNT];
+    int64_t acc_n[K_COUNT];
+    int64_t launches;
+};
+
+namespace {
+
+int set_err(fft3d_plan p, int status, const char *what, cudaError_t e = cudaSuccess)
+{
+    if (p) {
+        if (e != cudaSuccess)
+            snprintf(p->err, sizeof(p->err), "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+        else
+            snprintf(p->err, sizeof(p->err), "%s", what);
+    }
+    return status;
+}
+
+double pass_bytes(const fft3d_plan_s *p, int kind)
+{
+    const double lines = (double)p->n0 * (double)p->n1;
+    const double cplx = lines * (double)p->m1 * (double)p->csize;
+    const double real = lines * (double)p->n2 * (double)p->rsize;
+    return (kind == K_R2C_Z || kind == K_C2R_Z) ? cplx + real : 2.0 * cplx;
+}
+
+cudaEvent_t take_event(fft3d_plan p)
+{
+    if (!p->pool.empty()) {
+        cudaEvent_t e = p->pool.back();
+        p->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Launch one pass, optionally bracketed by profiling events.
+template <class F> int run_pass(fft3d_plan p, int kind, cudaStream_t st, F &&launch)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (p->profiling) {
+        a = take_event(p);
+        b = take_event(p);
+        if (!a || !b) return set_err(p, FFT3D_ERR_CUDA, "cudaEventCreate failed");
+        cudaError_t e = cudaEventRecord(a, st);
+        if (e != cudaSuccess) return set_err(p, FFT3D_ERR_CUDA, "cudaEventRecord", e);
+    }
+    cudaError_t e = launch();
+    if (e != cudaSuccess) {
+        char what[64];
+        snprintf(what, sizeof(what), "launch of pass %s", kPassName[kind]);
+        return set_err(p, FFT3D_ERR_CUDA, what, e);
+    }
+    ++p->launches;
+    if (p->profiling) {
+        e = cudaEventRecord(b, st);
+        if (e != cudaSuccess) return set_err(p, FFT3D_ERR_CUDA, "cudaEventRecord", e);
+        p->pending.push_back({kind, a, b});
+    }
+    return FFT3D_OK;
+}
+
+cudaError_t col_launch(const fft3d_plan_s *p, int L, const ColArgs &a, int64_t tiles, const void *tw,
+                       cudaStream_t st)
+{
+    return p->dtype == FFT3D_F32 ? col_launch_f32(L, a, tiles, tw, st) : col_launch_f64(L, a, tiles, tw, st);
+}
+
+// y-pass (axis 1) tiles: per k0 plane, ceil(M / W) tiles of the k2 < M
+// columns, then ceil(N0 / W) tiles of the k2 = M column (W planes each).
+ColArgs ypass_args(const fft3d_plan_s *p, CLayout src, CLayout dst, int inverse, int64_t *tiles)
+{
+    ColArgs a;
+    a.src = src;
+    a.dst = dst;
+    a.n0 = p->n0;
+    a.n1 = p->n1;
+    a.m = p->m;
+    a.axis = 1;
+    a.inverse = inverse;
+    const int64_t w = p->g1.per_block;
+    a.tiles_per_plane = (p->m + w - 1) / w;
+    a.tiles_main = p->n0 * a.tiles_per_plane;
+    *tiles = a.tiles_main + (p->n0 + w - 1) / w;
+    return a;
+}
+
+// x-pass (axis 0) tiles: W consecutive flat (k1, k2) columns each.
+ColArgs xpass_args(const fft3d_plan_s *p, CLayout src, CLayout dst, int inverse, int64_t *tiles)
+{
+    ColArgs a;
+    a.src = src;
+    a.dst = dst;
+    a.n0 = p->n0;
+    a.n1 = p->n1;
+    a.m = p->m;
+    a.axis = 0;
+    a.inverse = inverse;
+    const int64_t w = p->g0.per_block;
+    *tiles = (p->n1 * p->m1 + w - 1) / w;
+    a.tiles_main = *tiles;
+    a.tiles_per_plane = 0;
+    return a;
+}
+
+int check_exec(fft3d_plan p, const void *in, const void *out, bool real_in)
+{
+    if (!p) return FFT3D_ERR_NULL;
+    if (!in || !out) return set_err(p, FFT3D_ERR_NULL, "null data pointer");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_err(p, FFT3D_ERR_CUDA, "cudaGetDevice", e);
+    if (dev != p->device) return set_err(p, FFT3D_ERR_DEVICE, "current device is not the plan's device");
+    if (((uintptr_t)in % p->csize) != 0 || ((uintptr_t)out % p->csize) != 0)
+        return set_err(p, FFT3D_ERR_ALIGN, "data pointer not aligned to one complex element");
+    if (in != out) {
+        const size_t lines = (size_t)p->n0 * (size_t)p->n1;
+        const size_t rbytes = lines * (size_t)p->n2 * p->rsize;
+        const size_t cbytes = lines * (size_t)p->m1 * p->csize;
+        const size_t ib = real_in ? rbytes : cbytes;
+        const size_t ob = real_in ? cbytes : rbytes;
+        const uintptr_t i0 = (uintptr_t)in, o0 = (uintptr_t)out;
+        if (i0 < o0 + ob && o0 < i0 + ib)
+            return set_err(p, FFT3D_ERR_LAYOUT, "input and output overlap without being identical");
+    }
+    return FFT3D_OK;
+}
+
+// R2C pipeline: z (R2C with output scales) -> y -> x.
+int forward_pipeline(fft3d_plan p, const void *in, void *out, cudaStream_t st, double se, double sm)
+{
+    const CLayout L = {out, nullptr, 0};
+    ZArgs z;
+    z.real = in;
+    z.real_out = nullptr;
+    z.real_pitch = (in == out) ? 2 * p->m1 : p->n2;
+    z.cplx = L;
+    z.nlines = p->n0 * p->n1;
+    z.scale_edge = se;
+    z.scale_mid = sm;
+    int rc = run_pass(p, K_R2C_Z, st, [&] {
+        return p->dtype == FFT3D_F32 ? zr2c_launch_f32((int)p->m, z, p->twz, p->rot, st)
+                                     : zr2c_launch_f64((int)p->m, z, p->twz, p->rot, st);
+    });
+    if (rc) return rc;
+    if (p->n1 > 1) {
+        int64_t tiles;
+        const ColArgs a = ypass_args(p, L, L, 0, &tiles);
+        rc = run_pass(p, K_R2C_Y, st, [&] { return col_launch(p, (int)p->n1, a, tiles, p->tw1, st); });
+        if (rc) return rc;
+    }
+    if (p->n0 > 1) {
+        int64_t tiles;
+        const ColArgs a = xpass_args(p, L, L, 0, &tiles);
+        rc = run_pass(p, K_R2C_X, st, [&] { return col_launch(p, (int)p->n0, a, tiles, p->tw0, st); });
+        if (rc) return rc;
+    }
+    return FFT3D_OK;
+}
+
+// C2R pipeline: x -> y -> z (C2R with edge weight `we` and output scale `s`).
+// Out of place, the x-pass writes the split layout (k2 < M rows in the
+// output buffer, k2 = M in the plan's scratch plane) so the input survives.
+int inverse_pipeline(fft3d_plan p, const void *in, void *out, cudaStream_t st, double we, double s)
+{
+    const bool inplace = (in == out);
+    const CLayout src = {const_cast<void *>(in), nullptr, 0};
+    const CLayout dst = inplace ? src : CLayout{out, p->nyq, 1};
+    int rc;
+    if (p->n0 > 1 || !inplace) {
+        int64_t tiles;
+        const ColArgs a = xpass_args(p, src, dst, 1, &tiles);
+        rc = run_pass(p, K_C2R_X, st, [&] { return col_launch(p, (int)p->n0, a, tiles, p->tw0, st); });
+        if (rc) return rc;
+    }
+    if (p->n1 > 1) {
+        int64_t tiles;
+        const ColArgs a = ypass_args(p, dst, dst, 1, &tiles);
+        rc = run_pass(p, K_C2R_Y, st, [&] { return col_launch(p, (int)p->n1, a, tiles, p->tw1, st); });
+        if (rc) return rc;
+    }
+    ZArgs z;
+    z.real = nullptr;
+    z.real_out = out;
+    z.real_pitch = inplace ? 2 * p->m1 : p->n2;
+    z.cplx = dst;
+    z.nlines = p->n0 * p->n1;
+    z.scale_edge = we;
+    z.scale_mid = s;
+    return run_pass(p, K_C2R_Z, st, [&] {
+        return p->dtype == FFT3D_F32 ? zc2r_launch_f32((int)p->m, z, p->twz, p->rot, st)
+                                     : zc2r_launch_f64((int)p->m, z, p->twz, p->rot, st);
+    });
+}
+
+cudaError_t gen_line_tables(int dtype, int L, void *dst)
+{
+    for (int s = 1; s < line_nstages(L); ++s) {
+        const size_t off = (size_t)line_tw_offset(L, s) * (dtype == FFT3D_F32 ? 8 : 16);
+        void *o = (char *)dst + off;
+        const int ns = line_ns(L, s), r = line_radix(L, s);
+        cudaError_t e = dtype == FFT3D_F32 ? twiddle_stage_launch_f32(o, ns, r, 0)
+                                           : twiddle_stage_launch_f64(o, ns, r, 0);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fft3d_supported_length(int64_t n, int axis)
+{
+    if (axis == 0 || axis == 1) return col_supported(n) ? 1 : 0;
+    if (axis == 2) return (n >= 2 && n % 2 == 0 && z_half_supported(n / 2)) ? 1 : 0;
+    return 0;
+}
+
+int fft3d_plan_create(fft3d_plan *out, int64_t n0, int64_t n1, int64_t n2, int dtype)
+{
+    if (!out) return FFT3D_ERR_NULL;
+    *out = nullptr;
+    if (dtype != FFT3D_F32 && dtype != FFT3D_F64) return FFT3D_ERR_DTYPE;
+    if (!fft3d_supported_length(n0, 0) || !fft3d_supported_length(n1, 1) || !fft3d_supported_length(n2, 2))
+        return FFT3D_ERR_SIZE;
+    fft3d_plan p = new (std::nothrow) fft3d_plan_s();
+    if (!p) return FFT3D_ERR_ALLOC;
+    p->n0 = n0;
+    p->n1 = n1;
+    p->n2 = n2;
+    p->m = n2 / 2;
+    p->m1 = n2 / 2 + 1;
+    p->dtype = dtype;
+    p->rsize = dtype == FFT3D_F32 ? 4 : 8;
+    p->csize = 2 * p->rsize;
+    p->err[0] = 0;
+    int rc = FFT3D_OK;
+    cudaError_t e = cudaGetDevice(&p->device);
+    const bool f32 = dtype == FFT3D_F32;
+    if (e != cudaSuccess) {
+        rc = FFT3D_ERR_CUDA;
+        goto fail;
+    }
+    if (!(f32 ? col_geom_f32((int)n0, &p->g0) : col_geom_f64((int)n0, &p->g0)) ||
+        !(f32 ? col_geom_f32((int)n1, &p->g1) : col_geom_f64((int)n1, &p->g1)) ||
+        !(f32 ? z_geom_f32((int)p->m, &p->gz) : z_geom_f64((int)p->m, &p->gz))) {
+        rc = FFT3D_ERR_SIZE;
+        goto fail;
+    }
+    {
+        const size_t s0 = align256((size_t)line_tw_size((int)n0) * p->csize + 16);
+        const size_t s1 = align256((size_t)line_tw_size((int)n1) * p->csize + 16);
+        const size_t sz = align256((size_t)line_tw_size((int)p->m) * p->csize + 16);
+        const size_t sr = align256((size_t)p->m * p->csize);
+        e = cudaMalloc(&p->tw, s0 + s1 + sz + sr);
+        if (e != cudaSuccess) {
+            rc = FFT3D_ERR_ALLOC;
+            goto fail;
+        }
+        char *base = (char *)p->tw;
+        p->tw0 = base;
+        p->tw1 = base + s0;
+        p->twz = base + s0 + s1;
+        p->rot = base + s0 + s1 + sz;
+        if ((e = gen_line_tables(dtype, (int)n0, base)) != cudaSuccess ||
+            (e = gen_line_tables(dtype, (int)n1, base + s0)) != cudaSuccess ||
+            (e = gen_line_tables(dtype, (int)p->m, base + s0 + s1)) != cudaSuccess ||
+            (e = (f32 ? twiddle_rot_launch_f32 : twiddle_rot_launch_f64)(base + s0 + s1 + sz, (int)n2,
+                                                                         (int)p->m, 0)) != cudaSuccess) {
+            rc = FFT3D_ERR_CUDA;
+            goto fail;
+        }
+        e = cudaMalloc(&p->nyq, (size_t)n0 * (size_t)n1 * p->csize);
+        if (e != cudaSuccess) {
+            rc = FFT3D_ERR_ALLOC;
+            goto fail;
+        }
+        if ((e = (f32 ? col_prepare_f32 : col_prepare_f64)((int)n0)) != cudaSuccess ||
+            (e = (f32 ? col_prepare_f32 : col_prepare_f64)((int)n1)) != cudaSuccess ||
+            (e = (f32 ? z_prepare_f32 : z_prepare_f64)((int)p->m)) != cudaSuccess) {
+            rc = FFT3D_ERR_CUDA;
+            goto fail;
+        }
+        e = cudaStreamSynchronize(0);
+        if (e != cudaSuccess) {
+            rc = FFT3D_ERR_CUDA;
+            goto fail;
+        }
+    }
+    *out = p;
+    return FFT3D_OK;
+fail:
+    if (p->tw) cudaFree(p->tw);
+    if (p->nyq) cudaFree(p->nyq);
+    delete p;
+    (void)cudaGetLastError();
+    return rc;
+}
+
+int fft3d_plan_destroy(fft3d_plan p)
+{
+    if (!p) return FFT3D_OK;
+    for (auto &r : p->pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto ev : p->pool) cudaEventDestroy(ev);
+    cudaError_t e1 = p->tw ? cudaFree(p->tw) : cudaSuccess;
+    cudaError_t e2 = p->nyq ? cudaFree(p->nyq) : cudaSuccess;
+    delete p;
+    return (e1 == cudaSuccess && e2 == cudaSuccess) ? FFT3D_OK : FFT3D_ERR_CUDA;
+}
+
+int fft3d_exec_r2c(fft3d_plan p, const void *in_real, void *out_cplx, void *stream)
+{
+    int rc = check_exec(p, in_real, out_cplx, true);
+    if (rc) return rc;
+    return forward_pipeline(p, in_real, out_cplx, (cudaStream_t)stream, 1.0, 1.0);
+}
+
+int fft3d_exec_c2r(fft3d_plan p, const void *in_cplx, void *out_real, void *stream)
+{
+    int rc = check_exec(p, in_cplx, out_real, false);
+    if (rc) return rc;
+    const double s = 1.0 / ((double)p->n0 * (double)p->n1 * (double)p->n2);
+    return inverse_pipeline(p, in_cplx, out_real, (cudaStream_t)stream, 1.0, s);
+}
+
+int fft3d_exec_r2c_adjoint(fft3d_plan p, const void *in_cplx, void *out_real, void *stream)
+{
+    int rc = check_exec(p, in_cplx, out_real, false);
+    if (rc) return rc;
+    return inverse_pipeline(p, in_cplx, out_real, (cudaStream_t)stream, 2.0, 0.5);
+}
+
+int fft3d_exec_c2r_adjoint(fft3d_plan p, const void *in_real, void *out_cplx, void *stream)
+{
+    int rc = check_exec(p, in_real, out_cplx, true);
+    if (rc) return rc;
+    const double s = 1.0 / ((double)p->n0 * (double)p->n1 * (double)p->n2);
+    return forward_pipeline(p, in_real, out_cplx, (cudaStream_t)stream, s, 2.0 * s);
+}
+
+const char *fft3d_strerror(int status)
+{
+    switch (status) {
+    case FFT3D_OK: return "ok";
+    case FFT3D_ERR_SIZE: return "unsupported transform size";
+    case FFT3D_ERR_DTYPE: return "unsupported dtype";
+    case FFT3D_ERR_NULL: return "null pointer argument";
+    case FFT3D_ERR_ALIGN: return "data pointer not aligned to one complex element";
+    case FFT3D_ERR_ALLOC: return "allocation failed";
+    case FFT3D_ERR_CUDA: return "CUDA error";
+    case FFT3D_ERR_LAYOUT: return "input and output overlap without being identical";
+    case FFT3D_ERR_DEVICE: return "current device is not the plan's device";
+    case FFT3D_ERR_ARG: return "invalid argument";
+    default: return "unknown status";
+    }
+}
+
+const char *fft3d_plan_last_error(fft3d_plan p) { return p ? p->err : ""; }
+
+int fft3d_plan_set_profiling(fft3d_plan p, int enable)
+{
+    if (!p) return FFT3D_ERR_NULL;
+    p->profiling = enable ? 1 : 0;
+    return FFT3D_OK;
+}
+
+int fft3d_plan_profile_read(fft3d_plan p, fft3d_kernel_stat *stats, int max, int *count)
+{
+    if (!p || !count || (max > 0 && !stats)) return FFT3D_ERR_NULL;
+    int rc = FFT3D_OK;
+    for (auto &r : p->pending) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) {
+            rc = set_err(p, FFT3D_ERR_CUDA, "profile event", e);
+        } else {
+            p->acc_ms[r.kind] += ms;
+            p->acc_n[r.kind] += 1;
+        }
+        p->pool.push_back(r.a);
+        p->pool.push_back(r.b);
+    }
+    p->pending.clear();
+    int n = 0;
+    for (int k = 0; k < K_COUNT; ++k) {
+        if (p->acc_n[k] == 0) continue;
+        if (n < max) {
+            fft3d_kernel_stat &s = stats[n];
+            memset(&s, 0, sizeof(s));
+            snprintf(s.name, sizeof(s.name), "%s", kPassName[k]);
+            s.launches = p->acc_n[k];
+            s.total_ms = p->acc_ms[k];
+            s.bytes_per_launch = pass_bytes(p, k);
+        }
+        ++n;
+        p->acc_ms[k] = 0;
+        p->acc_n[k] = 0;
+    }
+    *count = n < max ? n : max;
+    return rc;
+}
+
+int fft3d_plan_launch_count(fft3d_plan p, int64_t *count)
+{
+    if (!p || !count) return FFT3D_ERR_NULL;
+    *count = p->launches;
+    return FFT3D_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,47 @@
+// Internal host-side launchers (C++; not part of the public C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pass_kernels.cuh"
+
+namespace fft3d {
+
+// X-macro lists of the compiled line lengths.
+#define FFT3D_COL_LENGTHS(X)                                                              \
+    X(1) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(3) X(6) \
+        X(12) X(24) X(48) X(96) X(192) X(384) X(768) X(1536)
+#define FFT3D_Z_HALF_LENGTHS(X)                                                          \
+    X(1) X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(3) X(6) X(12) \
+        X(24) X(48) X(96) X(192) X(384) X(768)
+
+// Launch geometry of one pass, for the plan to size grids and shared memory.
+struct PassGeom {
+    int threads;      // block size
+    int per_block;    // columns (colpass) or lines (zpass) per block
+    size_t smem;      // dynamic shared memory bytes
+};
+
+// dtype-specific entry points, defined in kern_f32.cu / kern_f64.cu.
+// Each returns cudaSuccess or the launch error.  `prepare` raises the
+// dynamic shared-memory limit of the kernels a plan will use on the current
+// device; `geom` reports the launch geometry.
+#define FFT3D_DECLARE_LAUNCHERS(SUF, R)                                                              \
+    bool col_geom_##SUF(int L, PassGeom *g);                                                         \
+    bool z_geom_##SUF(int M, PassGeom *g);                                                           \
+    cudaError_t col_prepare_##SUF(int L);                                                            \
+    cudaError_t z_prepare_##SUF(int M);                                                              \
+    cudaError_t col_launch_##SUF(int L, const ColArgs &a, int64_t tiles, const void *tw,            \
+                                 cudaStream_t st);                                                   \
+    cudaError_t zr2c_launch_##SUF(int M, const ZArgs &a, const void *tw, const void *rot,           \
+                                  cudaStream_t st);                                                  \
+    cudaError_t zc2r_launch_##SUF(int M, const ZArgs &a, const void *tw, const void *rot,           \
+                                  cudaStream_t st);                                                  \
+    cudaError_t twiddle_stage_launch_##SUF(void *out, int ns, int r, cudaStream_t st);             \
+    cudaError_t twiddle_rot_launch_##SUF(void *out, int n, int count, cudaStream_t st);
+
+FFT3D_DECLARE_LAUNCHERS(f32, float)
+FFT3D_DECLARE_LAUNCHERS(f64, double)
+
+}  // namespace fft3d

@@ -1,0 +1,233 @@
+// Register-resident Stockham line FFT: complex helpers, radix-2/3/4/8/16
+// butterflies and the stage engine used by every pass kernel.
+//
+// All butterflies compute the forward DFT y[k] = sum_n a[n] exp(-2 pi i n k / R)
+// (Eq. 1's sign).  Inverse transforms reuse them through
+// IDFT(x) = conj(DFT(conj(x))), applied when a pass loads and stores.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "line_plan.cuh"
+
+namespace fft3d {
+
+template <typename R> struct cvec;
+template <> struct cvec<float> { typedef float2 T; };
+template <> struct cvec<double> { typedef double2 T; };
+
+template <typename C> __device__ __forceinline__ C cmake(decltype(C::x) x, decltype(C::x) y)
+{
+    C r;
+    r.x = x;
+    r.y = y;
+    return r;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return cmake<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmake<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b)
+{
+    return cmake<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b)
+{
+    return cmake<C>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+// -i * a
+template <typename C> __device__ __forceinline__ C cmul_mi(C a) { return cmake<C>(a.y, -a.x); }
+template <typename C> __device__ __forceinline__ C cconj(C a) { return cmake<C>(a.x, -a.y); }
+template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return cmake<C>(a.x * s, a.y * s); }
+
+// cos(pi/8), sin(pi/8), sqrt(1/2), sqrt(3)/2
+#define FFT3D_C8 0.923879532511286756128183189396788933
+#define FFT3D_S8 0.382683432365089771728459984030398866
+#define FFT3D_R2 0.707106781186547524400844362104849039
+#define FFT3D_S3 0.866025403784438646763723170752936183
+
+template <int R, typename C> struct Dft;
+
+template <typename C> struct Dft<1, C> {
+    __device__ __forceinline__ static void run(C *) {}
+};
+
+template <typename C> struct Dft<2, C> {
+    __device__ __forceinline__ static void run(C *a)
+    {
+        const C t = a[0];
+        a[0] = cadd(t, a[1]);
+        a[1] = csub(t, a[1]);
+    }
+};
+
+template <typename C> struct Dft<3, C> {
+    __device__ __forceinline__ static void run(C *a)
+    {
+        typedef decltype(C::x) R;
+        const C t = cadd(a[1], a[2]);
+        const C u = csub(a[1], a[2]);
+        const C m = cmake<C>(a[0].x - R(0.5) * t.x, a[0].y - R(0.5) * t.y);
+        // -i * (sqrt(3)/2) * u
+        const C v = cmake<C>(R(FFT3D_S3) * u.y, -R(FFT3D_S3) * u.x);
+        a[0] = cadd(a[0], t);
+        a[1] = cadd(m, v);
+        a[2] = csub(m, v);
+    }
+};
+
+template <typename C> __device__ __forceinline__ void dft4(C &a0, C &a1, C &a2, C &a3)
+{
+    const C t0 = cadd(a0, a2);
+    const C t1 = csub(a0, a2);
+    const C t2 = cadd(a1, a3);
+    const C t3 = cmul_mi(csub(a1, a3));
+    a0 = cadd(t0, t2);
+    a2 = csub(t0, t2);
+    a1 = cadd(t1, t3);
+    a3 = csub(t1, t3);
+}
+
+template <typename C> struct Dft<4, C> {
+    __device__ __forceinline__ static void run(C *a) { dft4(a[0], a[1], a[2], a[3]); }
+};
+
+// z * exp(-2 pi i / 8) = z (1 - i) / sqrt 2
+template <typename C> __device__ __forceinline__ C w8_1(C z)
+{
+    typedef decltype(C::x) R;
+    return cmake<C>(R(FFT3D_R2) * (z.x + z.y), R(FFT3D_R2) * (z.y - z.x));
+}
+// z * exp(-2 pi i 3 / 8) = z (-1 - i) / sqrt 2
+template <typename C> __device__ __forceinline__ C w8_3(C z)
+{
+    typedef decltype(C::x) R;
+    return cmake<C>(R(FFT3D_R2) * (z.y - z.x), -R(FFT3D_R2) * (z.x + z.y));
+}
+
+template <typename C> struct Dft<8, C> {
+    // radix 2 x 4: even and odd halves, then one layer of radix-2
+    __device__ __forceinline__ static void run(C *a)
+    {
+        C e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+        C o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+        dft4(e0, e1, e2, e3);
+        dft4(o0, o1, o2, o3);
+        o1 = w8_1(o1);
+        o2 = cmul_mi(o2);
+        o3 = w8_3(o3);
+        a[0] = cadd(e0, o0);
+        a[4] = csub(e0, o0);
+        a[1] = cadd(e1, o1);
+        a[5] = csub(e1, o1);
+        a[2] = cadd(e2, o2);
+        a[6] = csub(e2, o2);
+        a[3] = cadd(e3, o3);
+        a[7] = csub(e3, o3);
+    }
+};
+
+template <typename C> struct Dft<16, C> {
+    // radix 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2;
+    // y[k1 + 4 k2] = sum_{n2} W16^{n2 k1} W4^{n2 k2} sum_{n1} a[4 n1 + n2] W4^{n1 k1}
+    __device__ __forceinline__ static void run(C *a)
+    {
+        typedef decltype(C::x) R;
+        dft4(a[0], a[4], a[8], a[12]);
+        dft4(a[1], a[5], a[9], a[13]);
+        dft4(a[2], a[6], a[10], a[14]);
+        dft4(a[3], a[7], a[11], a[15]);
+        // a[n2 + 4 k1] now holds the inner sum for (n2, k1); twiddle by W16^{n2 k1}
+        const C w1 = cmake<C>(R(FFT3D_C8), -R(FFT3D_S8));
+        const C w3 = cmake<C>(R(FFT3D_S8), -R(FFT3D_C8));
+        const C w9 = cmake<C>(-R(FFT3D_C8), R(FFT3D_S8));
+        a[5] = cmul(a[5], w1);     // n2=1, k1=1
+        a[9] = w8_1(a[9]);         // n2=1, k1=2 : W16^2
+        a[13] = cmul(a[13], w3);   // n2=1, k1=3
+        a[6] = w8_1(a[6]);         // n2=2, k1=1 : W16^2
+        a[10] = cmul_mi(a[10]);    // n2=2, k1=2 : W16^4
+        a[14] = w8_3(a[14]);       // n2=2, k1=3 : W16^6
+        a[7] = cmul(a[7], w3);     // n2=3, k1=1
+        a[11] = w8_3(a[11]);       // n2=3, k1=2 : W16^6
+        a[15] = cmul(a[15], w9);   // n2=3, k1=3
+        dft4(a[0], a[1], a[2], a[3]);
+        dft4(a[4], a[5], a[6], a[7]);
+        dft4(a[8], a[9], a[10], a[11]);
+        dft4(a[12], a[13], a[14], a[15]);
+        // a[4 k1 + k2] holds y[k1 + 4 k2]: transpose the 4x4 index
+        C t;
+        t = a[1]; a[1] = a[4]; a[4] = t;
+        t = a[2]; a[2] = a[8]; a[8] = t;
+        t = a[3]; a[3] = a[12]; a[12] = t;
+        t = a[6]; a[6] = a[9]; a[9] = t;
+        t = a[7]; a[7] = a[13]; a[13] = t;
+        t = a[11]; a[11] = a[14]; a[14] = t;
+    }
+};
+
+// One Stockham stage s of a length-L line.  Thread j holds v[i] = x[j + i NT].
+// Butterfly b = j + q NT (q < E / R) combines x[b + m L/R], m < R, which are
+// v[q + m E/R]; with k = b mod Ns it applies W_{Ns R}^{m k}, a radix-R DFT,
+// and writes y[(b / Ns) Ns R + k + m Ns].  Non-final stages write through the
+// exchange `ex` and read back x'[j + i NT]; the final stage's output slots
+// coincide with its input slots, so it stays in registers (natural order).
+template <typename R, int L, int S, class Ex>
+__device__ __forceinline__ void line_stage(typename cvec<R>::T *v, int j,
+                                           const typename cvec<R>::T *__restrict__ tw, Ex &ex)
+{
+    typedef typename cvec<R>::T C;
+    constexpr int E = line_E(L);
+    constexpr int NT = L / E;
+    constexpr int RS = line_radix(L, S);
+    constexpr int NS = line_ns(L, S);
+    constexpr int Q = E / RS;
+    constexpr bool LAST = (S == line_nstages(L) - 1);
+    constexpr int TWO = line_tw_offset(L, S);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int b = j + q * NT;
+        const int k = b % NS;
+        C t[RS];
+#pragma unroll
+        for (int m = 0; m < RS; ++m) t[m] = v[q + m * Q];
+        if (S > 0) {
+#pragma unroll
+            for (int m = 1; m < RS; ++m) t[m] = cmul(t[m], __ldg(tw + TWO + (m - 1) * NS + k));
+        }
+        Dft<RS, C>::run(t);
+        if (LAST) {
+#pragma unroll
+            for (int m = 0; m < RS; ++m) v[q + m * Q] = t[m];
+        } else {
+            const int base = (b / NS) * NS * RS + k;
+#pragma unroll
+            for (int m = 0; m < RS; ++m) ex.put(base + m * NS, t[m]);
+        }
+    }
+    if (!LAST) {
+        ex.sync();
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i] = ex.get(j + i * NT);
+        ex.sync();
+    }
+}
+
+template <typename R, int L, int S, class Ex>
+__device__ __forceinline__ void line_stages_from(typename cvec<R>::T *v, int j,
+                                                 const typename cvec<R>::T *__restrict__ tw, Ex &ex)
+{
+    if constexpr (S < line_nstages(L)) {
+        line_stage<R, L, S>(v, j, tw, ex);
+        line_stages_from<R, L, S + 1>(v, j, tw, ex);
+    }
+}
+
+// Forward FFT of a line held as v[i] = x[j + i NT]; result in the same slots.
+template <typename R, int L, class Ex>
+__device__ __forceinline__ void line_fft(typename cvec<R>::T *v, int j,
+                                         const typename cvec<R>::T *__restrict__ tw, Ex &ex)
+{
+    line_stages_from<R, L, 0>(v, j, tw, ex);
+}
+
+}  // namespace fft3d

@@ -1,0 +1,297 @@
+// Pass kernels of the 3D R2C / C2R transform.
+//
+//   zpass_r2c : forward, contiguous axis 2.  Each real line of N2 = 2M values
+//               is read as M complex pairs z[n] = x[2n] + i x[2n+1], given an
+//               M-point FFT Z, and turned into the N2/2 + 1 = M + 1 Hermitian
+//               half-spectrum entries X[k] = E[k] + W_N2^k O[k] with
+//               E = (Z[k] + conj Z[M-k]) / 2, O = (Z[k] - conj Z[M-k]) / 2i.
+//               (Step 1 of Sec. 3 along the first of the two plane axes.)
+//   zpass_c2r : inverse, contiguous axis 2: the same relation run backwards,
+//               then the M-point inverse FFT, the unpacking into 2M reals and
+//               the 1/(N0 N1 N2) normalisation (the paper's separate
+//               normalisation step, fused here).
+//   colpass   : C2C along a strided axis (axis 1, the second plane axis of
+//               Step 1; or axis 0, the slowest axis of Step 5).  A tile of W
+//               adjacent columns is read with the lanes of a warp across the
+//               columns, so every row of the tile is one coalesced segment of
+//               W * sizeof(complex) = 128 bytes; the column FFTs exchange
+//               through shared memory.  The x-pass does in one read and one
+//               write what the paper does with two transposes and an
+//               all-to-all (Steps 2-5): no transposed copy of the array exists.
+#pragma once
+
+#include "line_fft.cuh"
+
+namespace fft3d {
+
+// ------------------------------------------------------------ layouts
+// Complex half-spectrum array, logically [N0][N1][M + 1].
+//   standard: main[(k0 N1 + k1) (M + 1) + k2]
+//   split:    k2 < M  -> main[(k0 N1 + k1) M + k2]
+//             k2 == M -> nyq[k0 N1 + k1]
+// The split form lets an out-of-place inverse run in a dense real output
+// buffer (which has room for exactly M complex values per line) plus one
+// N0 x N1 plane of scratch for the k2 = M column.
+struct CLayout {
+    void *main;
+    void *nyq;
+    int split;
+};
+
+struct ColArgs {
+    CLayout src, dst;
+    int64_t n0, n1, m;        // grid N0, N1 and M = N2 / 2
+    int axis;                 // 0: rows are k0 (x-pass); 1: rows are k1 (y-pass)
+    int inverse;              // 1: exp(+...) via conj in / conj out
+    int64_t tiles_main;       // tiles of the main column set
+    int64_t tiles_per_plane;  // y-pass: main tiles per k0 plane
+};
+
+template <typename C>
+__device__ __forceinline__ void layout_column(const CLayout &l, int64_t n1, int64_t m, int axis,
+                                              int64_t k0, int64_t k1, int64_t k2, C *&ptr,
+                                              int64_t &stride)
+{
+    if (!l.split) {
+        ptr = (C *)l.main + ((k0 * n1 + k1) * (m + 1) + k2);
+        stride = axis == 0 ? n1 * (m + 1) : (m + 1);
+    } else if (k2 < m) {
+        ptr = (C *)l.main + ((k0 * n1 + k1) * m + k2);
+        stride = axis == 0 ? n1 * m : m;
+    } else {
+        ptr = (C *)l.nyq + (k0 * n1 + k1);
+        stride = axis == 0 ? n1 : 1;
+    }
+}
+
+// Column-tile exchange: element (row, column c) at sm[row * W + c].  With
+// W * sizeof(complex) = 128 bytes, each half/quarter-warp access is one row:
+// conflict-free without padding.
+template <typename C, int W> struct ColEx {
+    C *sm;
+    int c;
+    __device__ __forceinline__ void put(int row, C v) { sm[row * W + c] = v; }
+    __device__ __forceinline__ C get(int row) const { return sm[row * W + c]; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+
+template <typename R, int L, int W>
+__global__ void __launch_bounds__(W *(L / line_E(L)))
+colpass_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw)
+{
+    typedef typename cvec<R>::T C;
+    constexpr int E = line_E(L);
+    constexpr int NT = L / E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int c = threadIdx.x % W;
+    const int j = threadIdx.x / W;
+    const int64_t t = blockIdx.x;
+
+    // which column this lane owns
+    int64_t k0 = 0, k1 = 0, k2 = 0;
+    bool valid;
+    if (a.axis == 0) {
+        const int64_t f = t * W + c;  // flat (k1, k2) index
+        valid = f < a.n1 * (a.m + 1);
+        k1 = f / (a.m + 1);
+        k2 = f - k1 * (a.m + 1);
+    } else if (t < a.tiles_main) {
+        k0 = t / a.tiles_per_plane;
+        k2 = (t - k0 * a.tiles_per_plane) * W + c;
+        valid = k2 < a.m;
+    } else {  // k2 = M column of W consecutive planes
+        k0 = (t - a.tiles_main) * W + c;
+        k2 = a.m;
+        valid = k0 < a.n0;
+    }
+    C *sp = nullptr, *dp = nullptr;
+    int64_t ss = 0, ds = 0;
+    if (valid) {
+        layout_column<C>(a.src, a.n1, a.m, a.axis, k0, k1, k2, sp, ss);
+        layout_column<C>(a.dst, a.n1, a.m, a.axis, k0, k1, k2, dp, ds);
+    }
+
+    C v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        v[i] = valid ? sp[(int64_t)(j + i * NT) * ss] : cmake<C>(R(0), R(0));
+        if (a.inverse) v[i].y = -v[i].y;
+    }
+    ColEx<C, W> ex{(C *)smem_raw, c};
+    line_fft<R, L>(v, j, tw, ex);
+    if (valid) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            C o = v[i];
+            if (a.inverse) o.y = -o.y;
+            dp[(int64_t)(j + i * NT) * ds] = o;
+        }
+    }
+}
+
+// ------------------------------------------------------------ z pass
+struct ZArgs {
+    const void *real;     // real lines (read by r2c, written by c2r)
+    void *real_out;
+    int64_t real_pitch;   // line pitch of the real array, in real elements
+    CLayout cplx;         // half-spectrum lines (written by r2c, read by c2r)
+    int64_t nlines;       // N0 * N1
+    double scale_edge;    // r2c: factor on k2 = 0 and M outputs; c2r: weight of k2 = 0, M inputs
+    double scale_mid;     // r2c: factor on the other outputs;    c2r: output factor
+};
+
+// Per-line shared-memory exchange with one padding slot every 16 elements,
+// which makes the stride-16 writes of a radix-16 first stage conflict-free.
+template <typename C, int NT> struct LineEx {
+    C *sm;
+    __device__ __forceinline__ static int pad(int i) { return i + (i >> 4); }
+    __device__ __forceinline__ void put(int i, C v) { sm[pad(i)] = v; }
+    __device__ __forceinline__ C get(int i) const { return sm[pad(i)]; }
+    __device__ __forceinline__ void sync() const
+    {
+        if (NT <= 32) __syncwarp();
+        else __syncthreads();
+    }
+};
+
+template <int M> __host__ __device__ constexpr int zline_smem_elems() { return (M + 1) + ((M + 1) >> 4) + 1; }
+
+template <typename R, int M, int LPB>
+__global__ void __launch_bounds__(LPB *(M / line_E(M)))
+zpass_r2c_kernel(ZArgs a, const typename cvec<R>::T *__restrict__ tw,
+                 const typename cvec<R>::T *__restrict__ rot)
+{
+    typedef typename cvec<R>::T C;
+    constexpr int E = line_E(M);
+    constexpr int NT = M / E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lt = threadIdx.x / NT;
+    const int j = threadIdx.x % NT;
+    const int64_t line = (int64_t)blockIdx.x * LPB + lt;
+    const bool active = line < a.nlines;
+    LineEx<C, NT> ex{(C *)smem_raw + lt * zline_smem_elems<M>()};
+
+    const C *in = (const C *)((const R *)a.real + (active ? line : 0) * a.real_pitch);
+    C v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = active ? in[j + i * NT] : cmake<C>(R(0), R(0));
+
+    line_fft<R, M>(v, j, tw, ex);
+
+    // Hermitian post-process: needs Z[k] and Z[M - k] together
+#pragma unroll
+    for (int i = 0; i < E; ++i) ex.put(j + i * NT, v[i]);
+    ex.sync();
+    C *out = (C *)a.cplx.main + (active ? line : 0) * (M + 1);
+    const R se = R(a.scale_edge), sm = R(a.scale_mid);
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int k = j + i * NT;
+        const C z = ex.get(k);
+        const C zc = cconj(ex.get(k == 0 ? 0 : M - k));
+        const C s = cadd(z, zc);           // 2 E[k]
+        const C d = cmul(__ldg(rot + k), csub(z, zc));  // 2i W^k O[k]
+        // X[k] = (s - i d) / 2
+        const R f = R(0.5) * (k == 0 ? se : sm);
+        if (active) out[k] = cmake<C>(f * (s.x + d.y), f * (s.y - d.x));
+    }
+    if (active && j == 0) {
+        // X[M] = E[0] - O[0] = Re Z[0] - Im Z[0]
+        out[M] = cmake<C>(se * (v[0].x - v[0].y), R(0));
+    }
+}
+
+template <typename R, int M, int LPB>
+__global__ void __launch_bounds__(LPB *(M / line_E(M)))
+zpass_c2r_kernel(ZArgs a, const typename cvec<R>::T *__restrict__ tw,
+                 const typename cvec<R>::T *__restrict__ rot)
+{
+    typedef typename cvec<R>::T C;
+    constexpr int E = line_E(M);
+    constexpr int NT = M / E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lt = threadIdx.x / NT;
+    const int j = threadIdx.x % NT;
+    const int64_t line = (int64_t)blockIdx.x * LPB + lt;
+    const bool active = line < a.nlines;
+    LineEx<C, NT> ex{(C *)smem_raw + lt * zline_smem_elems<M>()};
+
+    const int64_t l = active ? line : 0;
+    const C *src;
+    const C *nyq;
+    if (a.cplx.split) {
+        src = (const C *)a.cplx.main + l * M;
+        nyq = (const C *)a.cplx.nyq + l;
+    } else {
+        src = (const C *)a.cplx.main + l * (M + 1);
+        nyq = src + M;
+    }
+    C v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = active ? src[j + i * NT] : cmake<C>(R(0), R(0));
+#pragma unroll
+    for (int i = 0; i < E; ++i) ex.put(j + i * NT, v[i]);
+    if (j == 0) ex.put(M, active ? *nyq : cmake<C>(R(0), R(0)));
+    ex.sync();
+
+    const R we = R(a.scale_edge);
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int k = j + i * NT;
+        C x = ex.get(k);
+        C y = ex.get(M - k);  // k = 0 pairs with X[M]
+        if (k == 0) {
+            // only the real parts of the k2 = 0 and k2 = M entries enter
+            x = cmake<C>(we * x.x, R(0));
+            y = cmake<C>(we * y.x, R(0));
+        }
+        const C yc = cconj(y);
+        const C e = cadd(x, yc);                      // E[k] (times 2)
+        const C o = cmulc(csub(x, yc), __ldg(rot + k));  // O[k] (times 2)
+        // Z = E + i O, kept conjugated for the inverse transform
+        v[i] = cmake<C>(e.x - o.y, -(e.y + o.x));
+    }
+    ex.sync();
+
+    line_fft<R, M>(v, j, tw, ex);
+
+    const R s = R(a.scale_mid);
+    C *out = (C *)((R *)a.real_out + l * a.real_pitch);
+    if (active) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) out[j + i * NT] = cmake<C>(s * v[i].x, -s * v[i].y);
+    }
+}
+
+// ------------------------------------------------------------ twiddles
+// Stage table of a line plan: entry (m - 1) * ns + k = exp(-2 pi i m k / (ns r)),
+// computed in FP64 with sincospi after exact integer reduction of m k, then
+// rounded once to the storage type.
+template <typename R>
+__global__ void twiddle_stage_kernel(typename cvec<R>::T *out, int ns, int r)
+{
+    typedef typename cvec<R>::T C;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (r - 1) * ns) return;
+    const int m = i / ns + 1;
+    const int k = i - (m - 1) * ns;
+    const int64_t d = (int64_t)ns * r;
+    const int64_t p = ((int64_t)m * k) % d;
+    double s, c;
+    sincospi(2.0 * (double)p / (double)d, &s, &c);
+    out[i] = cmake<C>(R(c), R(-s));
+}
+
+// rot[k] = exp(-2 pi i k / n), k < count (FP64 sincospi, rounded once)
+template <typename R>
+__global__ void twiddle_rot_kernel(typename cvec<R>::T *out, int n, int count)
+{
+    typedef typename cvec<R>::T C;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    double s, c;
+    sincospi(2.0 * (double)k / (double)n, &s, &c);
+    out[k] = cmake<C>(R(c), R(-s));
+}
+
+}  // namespace fft3d

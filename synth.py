@@ -77,11 +77,16 @@ def turbulence_spectrum(n0, n1, n2, seed, kmin=1.0, kmax=None, slope=-11.0 / 6.0
     k2 = np.arange(m1, dtype=np.float64)
     out = np.empty((n0, n1, m1), dtype=np.complex128)
     k12sq = k1[:, None] ** 2 + k2[None, :] ** 2
-    for i in range(n0):
-        kk = np.sqrt(k0[i] ** 2 + k12sq)
-        amp = np.where((kk >= kmin) & (kk <= kmax), np.power(np.maximum(kk, 1e-300), slope), 0.0)
-        phase = rng.uniform(0.0, 2.0 * np.pi, size=(n1, m1))
-        out[i] = amp * np.exp(1j * phase)
+    chunk = max(1, (1 << 22) // (n1 * m1))
+    for i in range(0, n0, chunk):
+        c = min(chunk, n0 - i)
+        kk = np.sqrt(k0[i:i + c, None, None] ** 2 + k12sq[None])
+        inside = (kk >= kmin) & (kk <= kmax)
+        amp = np.where(inside, np.power(np.where(inside, kk, 1.0), slope), 0.0)
+        # phases drawn plane after plane in C order (same stream for any chunk)
+        phase = rng.uniform(0.0, 2.0 * np.pi, size=(c, n1, m1))
+        out[i:i + c].real = amp * np.cos(phase)
+        out[i:i + c].imag = amp * np.sin(phase)
     return out
 
 
@@ -91,3 +96,28 @@ def random_half_spectrum(shape, seed):
     rng = np.random.default_rng(seed)
     m1 = n2 // 2 + 1
     return rng.standard_normal((n0, n1, m1)) + 1j * rng.standard_normal((n0, n1, m1))
+
+
+def turbulence_spectrum_device(n0, n1, n2, seed, device, kmin=1.0, kmax=None, slope=-11.0 / 6.0):
+    """Same recipe as ``turbulence_spectrum`` drawn on a CUDA device with
+    torch's seeded generator (the values differ from the numpy stream; the
+    distribution and structure are the same).  For timing runs, where a host
+    draw of ~1e9 modes would dominate the set-up time."""
+    import torch
+    if kmax is None:
+        kmax = min(n0, n1, n2) // 2
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    m1 = n2 // 2 + 1
+    k0 = torch.as_tensor(signed_wavenumbers(n0), dtype=torch.float64, device=device)
+    k1 = torch.as_tensor(signed_wavenumbers(n1), dtype=torch.float64, device=device)
+    k2 = torch.arange(m1, dtype=torch.float64, device=device)
+    out = torch.empty((n0, n1, m1), dtype=torch.complex128, device=device)
+    k12sq = k1[:, None] ** 2 + k2[None, :] ** 2
+    for i in range(n0):
+        kk = torch.sqrt(k0[i] ** 2 + k12sq)
+        inside = (kk >= kmin) & (kk <= kmax)
+        amp = torch.where(inside, torch.where(inside, kk, torch.ones_like(kk)) ** slope, torch.zeros_like(kk))
+        phase = torch.rand((n1, m1), generator=gen, dtype=torch.float64, device=device) * (2.0 * np.pi)
+        out[i] = torch.polar(amp, phase)
+    return out

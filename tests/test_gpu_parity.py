@@ -1,0 +1,137 @@
+"""CUDA path vs the FP64 oracle, element by element (relative L2 over all
+stored entries): <= 1e-13 for FP64 and <= 5e-6 for FP32, on seeded inputs.
+
+Sizes cover every compiled line length on each axis (several tiles and a
+ragged tail where the tile width does not divide the column count), both
+layouts (out-of-place dense, in-place padded), and the degenerate lengths 1
+and 2.  Runs on a GPU only."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import TOL, gpu_c2r, gpu_r2c, np_round, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+COL_LENGTHS = [1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048,
+               3, 6, 12, 24, 48, 96, 192, 384, 768, 1536]
+Z_HALF = [1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 3, 6, 12, 24, 48, 96, 192, 384, 768]
+
+SHAPES = sorted(set(
+    [(L, 6, 8) for L in COL_LENGTHS]
+    + [(4, L, 12) for L in COL_LENGTHS]
+    + [(3, 4, 2 * M) for M in Z_HALF]
+    + [(1, 1, 2), (2, 2, 2), (1, 4, 8), (4, 1, 8), (16, 16, 16), (24, 48, 96)]
+))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import paper_2202_12756_gb300 as fft3d
+    fft3d.load_library()
+
+
+def check_pair(shape, name, inplace, seed=0):
+    f = np_round(synth.uniform_field(shape, seed), name)
+    F_ref = oracle.rfft3(f)
+    F = gpu_r2c(f, name, inplace)
+    assert not np.isnan(F).any(), "unwritten output entries"
+    e1 = rel_l2(F, F_ref)
+    assert e1 <= TOL[name], (shape, name, inplace, "r2c", e1)
+    G = synth.random_half_spectrum(shape, seed + 100)
+    if name == "f32":
+        G = G.astype(np.complex64).astype(np.complex128)
+    g_ref = oracle.irfft3(G, shape)
+    g = gpu_c2r(G, shape, name, inplace)
+    assert not np.isnan(g).any(), "unwritten output entries"
+    e2 = rel_l2(g, g_ref)
+    assert e2 <= TOL[name], (shape, name, inplace, "c2r", e2)
+    return e1, e2
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("name", ["f64", "f32"])
+def test_parity_sweep_out_of_place(shape, name):
+    check_pair(shape, name, inplace=False)
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 4), (3, 4, 6), (64, 32, 48), (2048, 6, 8), (4, 1536, 12), (3, 4, 2048)],
+                         ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("name", ["f64", "f32"])
+def test_parity_in_place(shape, name):
+    check_pair(shape, name, inplace=True)
+
+
+@pytest.mark.parametrize("name", ["f64", "f32"])
+def test_config_64cubed(name):
+    """64^3, iid uniform[-1, 1) from seed 0, out-of-place and in-place."""
+    shape = (64, 64, 64)
+    f = np_round(synth.uniform_field(shape, 0), name)
+    F_ref = oracle.rfft3(f)
+    for inplace in (False, True):
+        F = gpu_r2c(f, name, inplace)
+        assert rel_l2(F, F_ref) <= TOL[name]
+        back = gpu_c2r(F_ref, shape, name, inplace)
+        assert rel_l2(back, f) <= TOL[name]
+
+
+def test_layouts_agree_bitwise():
+    shape = (32, 48, 64)
+    f = synth.uniform_field(shape, 3)
+    for name in ("f64", "f32"):
+        a = gpu_r2c(f, name, inplace=False)
+        b = gpu_r2c(f, name, inplace=True)
+        assert np.array_equal(a, b)
+        G = oracle.rfft3(f)
+        assert np.array_equal(gpu_c2r(G, shape, name, False), gpu_c2r(G, shape, name, True))
+
+
+def test_out_of_place_preserves_input():
+    import torch
+    import paper_2202_12756_gb300 as fft3d
+    shape = (24, 32, 48)
+    plan = fft3d.get_plan(shape, torch.float64, "cuda")
+    x = torch.from_numpy(synth.uniform_field(shape, 4)).cuda()
+    x0 = x.clone()
+    X = plan.r2c(x)
+    X0 = X.clone()
+    plan.c2r(X)
+    torch.cuda.synchronize()
+    assert torch.equal(x, x0)
+    assert torch.equal(X, X0)
+
+
+def test_eq5_field_closed_form_and_round_trip():
+    """Eq. 5 field: exact spectrum i (+-1) N^3 at (+-1, +-2, 3), (+-4, +-5, 6) and
+    the double-precision round trip at the 1e-14 level stated in Sec. 4."""
+    n = 64
+    f = synth.eq5_field(n, n, n)
+    F = gpu_r2c(f, "f64")
+    ref = np.zeros_like(F)
+    for (a0, a1, a2) in ((1, 2, 3), (4, 5, 6)):
+        for s0 in (1, -1):
+            for s1 in (1, -1):
+                ref[(s0 * a0) % n, (s1 * a1) % n, a2] = 1j * s0 * s1 * n ** 3
+    assert np.max(np.abs(F - ref)) < 1e-9 * n ** 3
+    back = gpu_c2r(F, (n, n, n), "f64")
+    assert np.max(np.abs(back - f)) / np.max(np.abs(f)) < 1e-14
+
+
+def test_plane_waves_512_fp64():
+    """512^3 FP64: uniform noise + 8 seeded plane waves, |k_i| < 256, seed 1.
+    Full oracle parity, and the wave part against its closed form."""
+    from oracle_pins import plane_wave_spectrum
+    shape = (512, 512, 512)
+    noise = synth.uniform_field(shape, 1)
+    kv = synth.plane_wave_vectors(1, count=8, kmax=256)
+    waves = synth.plane_waves(shape, kv)
+    f = noise + waves
+    F = gpu_r2c(f, "f64")
+    F_ref = oracle.rfft3(f)
+    assert rel_l2(F, F_ref) <= TOL["f64"]
+    F_noise = gpu_r2c(noise, "f64")
+    W = plane_wave_spectrum(shape, kv)
+    assert np.max(np.abs((F - F_noise) - W)) < 1e-9 * np.prod(shape)
+    back = gpu_c2r(F, shape, "f64")
+    assert rel_l2(back, f) <= TOL["f64"]
