@@ -151,6 +151,36 @@ int fft3d_plan_profile_read(fft3d_plan plan, fft3d_kernel_stat *stats, int max, 
 /* Kernel launches issued through this plan since creation. */
 int fft3d_plan_launch_count(fft3d_plan plan, int64_t *count);
 
+/*
+ * Normalised inverse C2R without a plan and without allocating anything.
+ * The paper has no counterpart; this entry point exists for callers that
+ * cannot call cudaMalloc: a program whose own pool allocator already holds
+ * the GPU's memory, or code that must not trigger the implicit device
+ * synchronisation cudaMalloc / cudaFree can cause.  fft3d_plan_create
+ * allocates, so these callers cannot make a plan.
+ *
+ * Computes exactly what fft3d_exec_c2r computes for a plan of
+ * (n0, n1, n2, dtype), with the same pass kernels, layouts, aliasing and
+ * alignment rules, on `stream`.  Instead of plan memory it uses one static
+ * device array of the library: FFT3D_NOALLOC_SCRATCH_BYTES for the
+ * N0 x N1 scratch plane plus 128 KiB of twiddle tables.  So:
+ *   - every GPU that loads the library holds that array until the process
+ *     exits;
+ *   - all calls share it and it keeps the last call's contents; calls that
+ *     overlap on the GPU (other streams, other host threads) race on it;
+ *   - nothing in it needs clearing: each call rewrites the tables, and the
+ *     scratch plane is written in full before it is read;
+ *   - the first call on a device performs set-up (cudaGetSymbolAddress of
+ *     the array and the kernels' shared-memory limits); make that first call
+ *     before any stream capture.
+ * Sizes beyond the array, n0 * n1 * (8 bytes for FFT3D_F32, 16 for
+ * FFT3D_F64) > FFT3D_NOALLOC_SCRATCH_BYTES, are rejected with FFT3D_ERR_SIZE
+ * before any work is queued, as are unsupported lengths.
+ */
+#define FFT3D_NOALLOC_SCRATCH_BYTES (8u << 20)
+int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64_t n0, int64_t n1, int64_t n2,
+                           int dtype, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -44,7 +44,7 @@ EXPORTED = (
     "fft3d_plan_create", "fft3d_plan_destroy", "fft3d_exec_r2c", "fft3d_exec_c2r",
     "fft3d_exec_r2c_adjoint", "fft3d_exec_c2r_adjoint", "fft3d_strerror",
     "fft3d_plan_last_error", "fft3d_supported_length", "fft3d_plan_set_profiling",
-    "fft3d_plan_profile_read", "fft3d_plan_launch_count",
+    "fft3d_plan_profile_read", "fft3d_plan_launch_count", "fft3d_exec_c2r_noalloc",
 )
 
 
@@ -82,6 +82,7 @@ def _declare(lib):
     lib.fft3d_plan_profile_read.argtypes = [P, ctypes.POINTER(KernelStat), ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_int)]
     lib.fft3d_plan_launch_count.argtypes = [P, ctypes.POINTER(I64)]
+    lib.fft3d_exec_c2r_noalloc.argtypes = [P, P, I64, I64, I64, ctypes.c_int, P]
     return lib
 
 
@@ -180,6 +181,13 @@ def fft3d_plan_launch_count(plan):
     c = ctypes.c_int64()
     _check(load_library().fft3d_plan_launch_count(plan, ctypes.byref(c)), "fft3d_plan_launch_count")
     return c.value
+
+
+def fft3d_exec_c2r_noalloc(in_cplx, out_real, n0, n1, n2, dtype, stream):
+    """Plan-free inverse C2R that allocates nothing (for callers that cannot
+    call cudaMalloc); see include/fft3d.h for the shared-scratch rules."""
+    _check(load_library().fft3d_exec_c2r_noalloc(in_cplx, out_real, n0, n1, n2, dtype, stream),
+           "fft3d_exec_c2r_noalloc")
 
 
 # ------------------------------------------------------------ torch layer

@@ -1,0 +1,185 @@
+// fft3d_exec_c2r_noalloc: the normalised inverse C2R without a plan and
+// without any device allocation.
+//
+// Who needs it: callers that cannot call cudaMalloc.  One kind has handed all
+// of the GPU's memory to its own pool allocator up front (a spectral solver
+// sizing its fields to fill HBM, say), so any cudaMalloc made by a library
+// fails or breaks the pool's budget.  Another kind runs where an implicit
+// device synchronisation is not allowed; cudaMalloc and cudaFree may
+// synchronise the device.  Such callers cannot create a plan
+// (fft3d_plan_create allocates its twiddle tables and its scratch plane with
+// cudaMalloc).
+//
+// Instead of plan memory, this file keeps one file-scope device array,
+// g_noalloc_scratch.  Each call writes the twiddle tables for its sizes into
+// it and uses the rest as the N0 x N1 scratch plane that holds the k2 = N2/2
+// column during an out-of-place inverse.  The pass kernels are the same as
+// for fft3d_exec_c2r.
+//
+// Rules, also stated in include/fft3d.h:
+//  * The array is a static device allocation of the library.  Every GPU that
+//    loads the library holds it until the process exits.
+//  * All calls share it.  Calls that overlap on the GPU (two streams, or two
+//    host threads) race on it and corrupt each other's results.
+//  * Nothing in it has to start at zero: every call rewrites the tables, and
+//    the x-pass writes the whole scratch plane before the y-pass reads it.
+//  * The first call on a device does the set-up: it fetches the array's
+//    device address with cudaGetSymbolAddress and raises the shared-memory
+//    limit of every pass kernel.  Make that first call before any stream
+//    capture.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "fft3d.h"
+#include "launchers.h"
+
+using namespace fft3d;
+
+namespace {
+
+// Twiddle space: four tables (axis 0, axis 1, axis 2 half length, R2C
+// rotation) of at most 2048 complex double entries each.
+constexpr size_t kTableSlot = 2048 * 16;
+constexpr size_t kTableBytes = 4 * kTableSlot;
+constexpr size_t kPlaneBytes = FFT3D_NOALLOC_SCRATCH_BYTES;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kTableBytes + kPlaneBytes];
+
+constexpr int kMaxDevices = 128;
+std::mutex g_setup_mu;
+void *g_scratch_ptr[kMaxDevices];  // device address of g_noalloc_scratch, per device
+
+#define FFT3D_NA_PREP(L)                                                   \
+    if ((e = col_prepare_f32(L)) != cudaSuccess) return e;                 \
+    if ((e = col_prepare_f64(L)) != cudaSuccess) return e;
+#define FFT3D_NA_PREP_Z(M)                                                 \
+    if ((e = z_prepare_f32(M)) != cudaSuccess) return e;                   \
+    if ((e = z_prepare_f64(M)) != cudaSuccess) return e;
+
+cudaError_t prepare_all_kernels()
+{
+    cudaError_t e;
+    FFT3D_COL_LENGTHS(FFT3D_NA_PREP)
+    FFT3D_Z_HALF_LENGTHS(FFT3D_NA_PREP_Z)
+    return cudaSuccess;
+}
+
+// Device address of the scratch array on the current device; the first call
+// per device looks it up and prepares the kernels.
+cudaError_t scratch_for_current_device(void **out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_setup_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        e = prepare_all_kernels();
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+cudaError_t write_line_tables(bool f32, int L, void *dst, cudaStream_t st)
+{
+    for (int s = 1; s < line_nstages(L); ++s) {
+        void *o = (char *)dst + (size_t)line_tw_offset(L, s) * (f32 ? 8 : 16);
+        cudaError_t e = f32 ? twiddle_stage_launch_f32(o, line_ns(L, s), line_radix(L, s), st)
+                            : twiddle_stage_launch_f64(o, line_ns(L, s), line_radix(L, s), st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64_t n0, int64_t n1,
+                                      int64_t n2, int dtype, void *stream)
+{
+    if (dtype != FFT3D_F32 && dtype != FFT3D_F64) return FFT3D_ERR_DTYPE;
+    if (!fft3d_supported_length(n0, 0) || !fft3d_supported_length(n1, 1) || !fft3d_supported_length(n2, 2))
+        return FFT3D_ERR_SIZE;
+    const bool f32 = dtype == FFT3D_F32;
+    const size_t csize = f32 ? 8 : 16;
+    if ((size_t)n0 * (size_t)n1 * csize > kPlaneBytes) return FFT3D_ERR_SIZE;  // beyond the scratch plane
+    if (!in_cplx || !out_real) return FFT3D_ERR_NULL;
+    if ((uintptr_t)in_cplx % csize || (uintptr_t)out_real % csize) return FFT3D_ERR_ALIGN;
+    const int64_t m = n2 / 2, m1 = m + 1;
+    if (in_cplx != out_real) {
+        const size_t lines = (size_t)n0 * (size_t)n1;
+        const size_t ib = lines * (size_t)m1 * csize, ob = lines * (size_t)n2 * (csize / 2);
+        const uintptr_t i0 = (uintptr_t)in_cplx, o0 = (uintptr_t)out_real;
+        if (i0 < o0 + ob && o0 < i0 + ib) return FFT3D_ERR_LAYOUT;
+    }
+    PassGeom g0, g1;
+    if (!(f32 ? col_geom_f32((int)n0, &g0) : col_geom_f64((int)n0, &g0)) ||
+        !(f32 ? col_geom_f32((int)n1, &g1) : col_geom_f64((int)n1, &g1)))
+        return FFT3D_ERR_SIZE;
+
+    void *scratch = nullptr;
+    if (scratch_for_current_device(&scratch) != cudaSuccess) return FFT3D_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *tw0 = (char *)scratch;
+    char *tw1 = tw0 + kTableSlot;
+    char *twz = tw1 + kTableSlot;
+    char *rot = twz + kTableSlot;
+    void *plane = (char *)scratch + kTableBytes;
+
+    cudaError_t e;
+    if ((e = write_line_tables(f32, (int)n0, tw0, st)) != cudaSuccess ||
+        (e = write_line_tables(f32, (int)n1, tw1, st)) != cudaSuccess ||
+        (e = write_line_tables(f32, (int)m, twz, st)) != cudaSuccess ||
+        (e = (f32 ? twiddle_rot_launch_f32 : twiddle_rot_launch_f64)(rot, (int)n2, (int)m, st)) != cudaSuccess)
+        return FFT3D_ERR_CUDA;
+
+    const bool inplace = in_cplx == out_real;
+    const CLayout src = {const_cast<void *>(in_cplx), nullptr, 0};
+    const CLayout dst = inplace ? src : CLayout{out_real, plane, 1};
+
+    if (n0 > 1 || !inplace) {  // x-pass: axis 0, W flat (k1, k2) columns per tile
+        ColArgs a;
+        a.src = src;
+        a.dst = dst;
+        a.n0 = n0;
+        a.n1 = n1;
+        a.m = m;
+        a.axis = 0;
+        a.inverse = 1;
+        const int64_t tiles = (n1 * m1 + g0.per_block - 1) / g0.per_block;
+        a.tiles_main = tiles;
+        a.tiles_per_plane = 0;
+        e = f32 ? col_launch_f32((int)n0, a, tiles, tw0, st) : col_launch_f64((int)n0, a, tiles, tw0, st);
+        if (e != cudaSuccess) return FFT3D_ERR_CUDA;
+    }
+    if (n1 > 1) {  // y-pass: axis 1, k2 < M tiles per plane, then the k2 = M column
+        ColArgs a;
+        a.src = dst;
+        a.dst = dst;
+        a.n0 = n0;
+        a.n1 = n1;
+        a.m = m;
+        a.axis = 1;
+        a.inverse = 1;
+        a.tiles_per_plane = (m + g1.per_block - 1) / g1.per_block;
+        a.tiles_main = n0 * a.tiles_per_plane;
+        const int64_t tiles = a.tiles_main + (n0 + g1.per_block - 1) / g1.per_block;
+        e = f32 ? col_launch_f32((int)n1, a, tiles, tw1, st) : col_launch_f64((int)n1, a, tiles, tw1, st);
+        if (e != cudaSuccess) return FFT3D_ERR_CUDA;
+    }
+    ZArgs z;
+    z.real = nullptr;
+    z.real_out = out_real;
+    z.real_pitch = inplace ? 2 * m1 : n2;
+    z.cplx = dst;
+    z.nlines = n0 * n1;
+    z.scale_edge = 1.0;
+    z.scale_mid = 1.0 / ((double)n0 * (double)n1 * (double)n2);
+    e = f32 ? zc2r_launch_f32((int)m, z, twz, rot, st) : zc2r_launch_f64((int)m, z, twz, rot, st);
+    return e == cudaSuccess ? FFT3D_OK : FFT3D_ERR_CUDA;
+}
