@@ -93,7 +93,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except OSError:
@@ -154,19 +154,20 @@ def max_over_ranks(x, pg, device=None):
     return float(t.item())
 
 
-def make_field(n, dev):
+def make_field(grid, dev):
     """Turbulence-like field of the headline workload, FP64 on the device,
     padded in-place layout, unit RMS."""
     import torch
 
     import synth
     import paper_2202_12756_gb300 as fft3d
-    plan64 = fft3d.get_plan((n, n, n), torch.float64, dev)
+    n0, n1, n2 = grid
+    plan64 = fft3d.get_plan(grid, torch.float64, dev)
     buf = plan64.empty_padded()
     spec = buf.view(torch.complex128)
-    spec.copy_(synth.turbulence_spectrum_device(n, n, n, seed=2, device=dev))
+    spec.copy_(synth.turbulence_spectrum_device(n0, n1, n2, seed=2, device=dev))
     plan64.c2r_(buf)
-    view = buf[..., :n]
+    view = buf[..., :n2]
     rms = torch.sqrt(torch.mean(view * view))
     view.div_(rms)
     torch.cuda.synchronize(dev)
@@ -234,6 +235,12 @@ def cpu_baseline(budget_s=12.0, n=256):
             "sample": f"{pairs} FP64 R2C+C2R pairs of a {n}^3 uniform field ({dt:.1f} s)"}
 
 
+def round_trip_error(plan, host_in, host_out):
+    """Relative L2 error of the last e2e step's round trip (host tensors)."""
+    d = (host_out.double() - host_in.double()).norm() / host_in.double().norm()
+    return float(d)
+
+
 def run_reference(args):
     world, rank, local, pg = dist_setup(args)
     if rank != 0:
@@ -269,12 +276,13 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     import paper_2202_12756_gb300 as fft3d
     fft3d.load_library()
-    n = args.n
+    grid = tuple(int(x) for x in args.grid.split(",")) if args.grid else (args.n,) * 3
+    n0, n1, n = grid
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"]
 
-    plan64, buf64 = make_field(n, dev)
-    plan32 = fft3d.get_plan((n, n, n), torch.float32, dev)
+    plan64, buf64 = make_field(grid, dev)
+    plan32 = fft3d.get_plan(grid, torch.float32, dev)
     buf32 = plan32.empty_padded()
     buf32.copy_(buf64)
 
@@ -285,27 +293,37 @@ def run_ours(args):
     clk = clocks.stop()
     ms32 = max_over_ranks(ms32, pg, dev)
     t_step = ms32 / args.steps
-    flops = pair_flops(n, n, n)
-    bytes_pair = 2 * pass_bytes(n, n, n, 4)
+    flops = pair_flops(n0, n1, n)
+    bytes_pair = 2 * pass_bytes(n0, n1, n, 4)
     value = flops * world / (t_step * 1e-3) / 1e9
 
     # ---- FP64 pair (same field)
-    ms64, launches64, stats64 = time_pairs(plan64, buf64, max(2, args.steps // 4), args.warmup, dev, pg,
-                                           profile=True)
+    steps64 = max(2, args.steps // 10)
+    ms64, launches64, stats64 = time_pairs(plan64, buf64, steps64, args.warmup, dev, pg, profile=True)
     ms64 = max_over_ranks(ms64, pg, dev)
-    t64 = ms64 / max(2, args.steps // 4)
+    t64 = ms64 / steps64
+    del buf64
 
-    # ---- end to end through the public API: pinned host in, pinned host out
-    host_in = torch.empty((n, n, n), dtype=torch.float32, pin_memory=True)
+    # ---- end to end through the public API: a dense field in pinned host
+    # memory goes to the device, through the out-of-place forward and inverse
+    # (the inverse leaves the spectrum intact), and back to pinned host memory
+    host_in = torch.empty(grid, dtype=torch.float32, pin_memory=True)
     host_in.copy_(buf32[..., :n])
     host_out = torch.empty_like(host_in, pin_memory=True)
+    del buf32
+    dev_real = plan32.empty_real()
+    dev_cplx = plan32.empty_complex()
     stream = torch.cuda.current_stream(dev)
-    e2e_steps = max(2, args.steps // 4)
+    e2e_steps = max(2, args.steps // 10)
+
+    def e2e_step():
+        dev_real.copy_(host_in, non_blocking=True)
+        plan32.r2c(dev_real, dev_cplx)
+        plan32.c2r(dev_cplx, dev_real)
+        host_out.copy_(dev_real, non_blocking=True)
+
     for _ in range(2):
-        buf32[..., :n].copy_(host_in, non_blocking=True)
-        plan32.r2c_(buf32)
-        plan32.c2r_(buf32)
-        host_out.copy_(buf32[..., :n], non_blocking=True)
+        e2e_step()
     torch.cuda.synchronize(dev)
     if pg is not None:
         pg.barrier()
@@ -313,33 +331,31 @@ def run_ours(args):
     b = torch.cuda.Event(enable_timing=True)
     a.record(stream)
     for _ in range(e2e_steps):
-        buf32[..., :n].copy_(host_in, non_blocking=True)
-        plan32.r2c_(buf32)
-        plan32.c2r_(buf32)
-        host_out.copy_(buf32[..., :n], non_blocking=True)
+        e2e_step()
     b.record(stream)
     torch.cuda.synchronize(dev)
     ms_e2e = max_over_ranks(a.elapsed_time(b), pg, dev) / e2e_steps
     e2e_val = flops * world / (ms_e2e * 1e-3) / 1e9
-    io_bytes = n * n * n * 4
+    io_bytes = n0 * n1 * n * 4
 
-    traffic = ncu_traffic(f"{n}^3 f32")
+    gname = f"{n0}x{n1}x{n}"
+    traffic = ncu_traffic(f"{gname} f32")
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"{n}^3 real grid, R2C+C2R pair in place (padded rows), FP32, "
+        "config": {"workload": f"{gname} real grid, R2C+C2R pair in place (padded rows), FP32, "
                                f"turbulence-like field (|k|^-11/6, seed 2)",
-                   "grid": [n, n, n], "layout": "in-place padded", "parallelism": f"replicas x{world}",
-                   "l2": "inputs (4.3 GB) larger than L2, no flush"},
+                   "grid": list(grid), "layout": "in-place padded", "parallelism": f"replicas x{world}",
+                   "l2": f"inputs ({n0 * n1 * (n // 2 + 1) * 8 / 1e9:.2f} GB) larger than L2, no flush"},
         "hbm_gbs": round(bytes_pair / (t_step * 1e-3) / 1e9, 1),
         "hbm_frac_of_peak": round(bytes_pair / (t_step * 1e-3) / 1e9 / peak, 4),
         "gflops_paper_convention": round(2 * value, 1),
         "roofline": roofline_from(stats32, peak, traffic),
         "fp64": {"ms_per_step": round(t64, 3),
                  "gflops": round(flops * world / (t64 * 1e-3) / 1e9, 1),
-                 "hbm_gbs": round(2 * pass_bytes(n, n, n, 8) / (t64 * 1e-3) / 1e9, 1),
+                 "hbm_gbs": round(2 * pass_bytes(n0, n1, n, 8) / (t64 * 1e-3) / 1e9, 1),
                  "per_pass_ms": {s["name"]: round(s["total_ms"] / s["launches"], 3) for s in stats64},
                  "fp32_speedup": round(t64 / t_step, 2)},
         "e2e": {"value": round(e2e_val, 1), "unit": UNIT, "ms_per_step": round(ms_e2e, 3),
@@ -348,6 +364,8 @@ def run_ours(args):
         "clocks": clk,
         "peak_source": peaks["src"],
     }
+    rt = round_trip_error(plan32, host_in, host_out)
+    line["fp32_round_trip_rel_l2"] = rt
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -360,10 +378,12 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--grid", type=str, default=None,
+                    help="N0,N1,N2 instead of N^3 (profiling and smaller cases)")
     ap.add_argument("--ref-n", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

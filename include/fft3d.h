@@ -152,6 +152,42 @@ int fft3d_plan_profile_read(fft3d_plan plan, fft3d_kernel_stat *stats, int max, 
 int fft3d_plan_launch_count(fft3d_plan plan, int64_t *count);
 
 /*
+ * Fused plane pass (opt-in).  For float plans with (N1, N2/2) in
+ * {(512, 256), (768, 384), (1024, 512), (1536, 768), (2048, 1024)}, axes 2
+ * and 1 can run as one persistent kernel that hands each k0 plane from the
+ * line transforms to the column transforms through L2, so HBM sees one read
+ * and one write of the array for both axes instead of two each.  Blocks in it
+ * wait on per-plane counters set by other blocks.  Off by default: on GB300
+ * at 1024^3 these passes are bound by instruction issue rather than HBM, and
+ * the fused kernel is slower than the separate passes.  Returns
+ * FFT3D_ERR_SIZE when the plan's shape or dtype has no fused kernel.
+ */
+int fft3d_plan_set_fused(fft3d_plan plan, int enable);
+
+/*
+ * Device-side error flag of the plan's fused plane pass (see
+ * fft3d_plan_set_fused), whose blocks wait on per-plane counters.
+ * Each such wait is bounded; a wait that runs out makes every block of that
+ * launch stop early (the output is then invalid) and sets this flag.
+ * fft3d_plan_status synchronises the device, stores the flag (0 or 1) in
+ * *device_error and clears it.  Plans without the fused pass always report 0.
+ */
+int fft3d_plan_status(fft3d_plan plan, int *device_error);
+
+/*
+ * Test hook for the bounded waits above: with inject_stall != 0 every
+ * waiting block waits for one producer more than exists, so its wait runs
+ * out after `spin_limit` polls (about 0.1 us each; <= 0 restores the default
+ * of about one second) and fft3d_plan_status then reports the error.  Keep
+ * inject_stall = 0 outside such tests.
+ */
+int fft3d_plan_set_debug(fft3d_plan plan, int inject_stall, int64_t spin_limit);
+
+/* *fused_plane_pass = 1 when the plan currently runs axes 2 and 1 as one
+ * fused pass (fft3d_plan_set_fused), else 0. */
+int fft3d_plan_info(fft3d_plan plan, int *fused_plane_pass);
+
+/*
  * Normalised inverse C2R without a plan and without allocating anything.
  * The paper has no counterpart; this entry point exists for callers that
  * cannot call cudaMalloc: a program whose own pool allocator already holds

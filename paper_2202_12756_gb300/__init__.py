@@ -45,6 +45,7 @@ EXPORTED = (
     "fft3d_exec_r2c_adjoint", "fft3d_exec_c2r_adjoint", "fft3d_strerror",
     "fft3d_plan_last_error", "fft3d_supported_length", "fft3d_plan_set_profiling",
     "fft3d_plan_profile_read", "fft3d_plan_launch_count", "fft3d_exec_c2r_noalloc",
+    "fft3d_plan_status", "fft3d_plan_set_debug", "fft3d_plan_info", "fft3d_plan_set_fused",
 )
 
 
@@ -83,6 +84,10 @@ def _declare(lib):
                                             ctypes.POINTER(ctypes.c_int)]
     lib.fft3d_plan_launch_count.argtypes = [P, ctypes.POINTER(I64)]
     lib.fft3d_exec_c2r_noalloc.argtypes = [P, P, I64, I64, I64, ctypes.c_int, P]
+    lib.fft3d_plan_status.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
+    lib.fft3d_plan_set_debug.argtypes = [P, ctypes.c_int, I64]
+    lib.fft3d_plan_info.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
+    lib.fft3d_plan_set_fused.argtypes = [P, ctypes.c_int]
     return lib
 
 
@@ -181,6 +186,28 @@ def fft3d_plan_launch_count(plan):
     c = ctypes.c_int64()
     _check(load_library().fft3d_plan_launch_count(plan, ctypes.byref(c)), "fft3d_plan_launch_count")
     return c.value
+
+
+def fft3d_plan_status(plan):
+    """Device error flag (0/1) of the plan's bounded waits; synchronises and clears it."""
+    v = ctypes.c_int()
+    _check(load_library().fft3d_plan_status(plan, ctypes.byref(v)), "fft3d_plan_status", plan)
+    return v.value
+
+
+def fft3d_plan_set_debug(plan, inject_stall, spin_limit=0):
+    _check(load_library().fft3d_plan_set_debug(plan, 1 if inject_stall else 0, int(spin_limit)),
+           "fft3d_plan_set_debug")
+
+
+def fft3d_plan_info(plan):
+    v = ctypes.c_int()
+    _check(load_library().fft3d_plan_info(plan, ctypes.byref(v)), "fft3d_plan_info")
+    return {"fused_plane_pass": bool(v.value)}
+
+
+def fft3d_plan_set_fused(plan, enable):
+    _check(load_library().fft3d_plan_set_fused(plan, 1 if enable else 0), "fft3d_plan_set_fused", plan)
 
 
 def fft3d_exec_c2r_noalloc(in_cplx, out_real, n0, n1, n2, dtype, stream):
@@ -326,6 +353,19 @@ class Plan:
 
     def launch_count(self):
         return fft3d_plan_launch_count(self.handle)
+
+    def status(self):
+        with _torch().cuda.device(self.device):
+            return fft3d_plan_status(self.handle)
+
+    def set_debug(self, inject_stall, spin_limit=0):
+        fft3d_plan_set_debug(self.handle, inject_stall, spin_limit)
+
+    def info(self):
+        return fft3d_plan_info(self.handle)
+
+    def set_fused(self, enable):
+        fft3d_plan_set_fused(self.handle, enable)
 
 
 _plans = {}

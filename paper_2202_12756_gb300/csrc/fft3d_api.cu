@@ -22,8 +22,11 @@ using namespace fft3d;
 
 namespace {
 
-enum PassKind { K_R2C_Z = 0, K_R2C_Y, K_R2C_X, K_C2R_X, K_C2R_Y, K_C2R_Z, K_COUNT };
-const char *const kPassName[K_COUNT] = {"r2c.z", "r2c.y", "r2c.x", "c2r.x", "c2r.y", "c2r.z"};
+enum PassKind { K_R2C_Z = 0, K_R2C_Y, K_R2C_X, K_C2R_X, K_C2R_Y, K_C2R_Z, K_R2C_ZY, K_C2R_YZ, K_COUNT };
+const char *const kPassName[K_COUNT] = {"r2c.z", "r2c.y", "r2c.x", "c2r.x", "c2r.y", "c2r.z", "r2c.zy", "c2r.yz"};
+
+// default bound on a fused-pass consumer's polls (each sleeps ~0.1 us): ~1 s
+constexpr long long kDefaultSpinLimit = 1LL << 23;
 
 // half length M = N2 / 2 of the contiguous axis: 2^k <= 1024 or 3 * 2^k <= 768
 bool z_half_supported(int64_t m)
@@ -46,8 +49,16 @@ struct fft3d_plan_s {
     size_t rsize, csize;  // bytes of one real / one complex element
     void *tw;             // device: all twiddle tables
     const void *tw0, *tw1, *twz, *rot;
+    const void *tw1f;     // axis-1 twiddles laid out for the fused kernel
     void *nyq;            // device: [n0][n1] complex scratch (k2 = M column)
     PassGeom g0, g1, gz;
+    int fused;            // plane pass fused (opt-in)
+    int fused_ok;         // the shape and dtype allow the fused plane pass
+    PassGeom gf;          // fused geometry (per_block = W of its Y tiles)
+    int fz_lines;         // lines per fused Z item
+    unsigned *sync;       // device: fused-pass tickets, flags, per-plane counters
+    long long spin_limit;
+    int inject_stall;
     char err[512];
     int profiling;
     struct Rec {
@@ -79,7 +90,8 @@ double pass_bytes(const fft3d_plan_s *p, int kind)
     const double lines = (double)p->n0 * (double)p->n1;
     const double cplx = lines * (double)p->m1 * (double)p->csize;
     const double real = lines * (double)p->n2 * (double)p->rsize;
-    return (kind == K_R2C_Z || kind == K_C2R_Z) ? cplx + real : 2.0 * cplx;
+    return (kind == K_R2C_Z || kind == K_C2R_Z || kind == K_R2C_ZY || kind == K_C2R_YZ) ? cplx + real
+                                                                                        : 2.0 * cplx;
 }
 
 cudaEvent_t take_event(fft3d_plan p)
@@ -141,6 +153,7 @@ ColArgs ypass_args(const fft3d_plan_s *p, CLayout src, CLayout dst, int inverse,
     const int64_t w = p->g1.per_block;
     a.tiles_per_plane = (p->m + w - 1) / w;
     a.tiles_main = p->n0 * a.tiles_per_plane;
+    a.nyq_in_plane = 0;
     *tiles = a.tiles_main + (p->n0 + w - 1) / w;
     return a;
 }
@@ -160,7 +173,44 @@ ColArgs xpass_args(const fft3d_plan_s *p, CLayout src, CLayout dst, int inverse,
     *tiles = (p->n1 * p->m1 + w - 1) / w;
     a.tiles_main = *tiles;
     a.tiles_per_plane = 0;
+    a.nyq_in_plane = 0;
     return a;
+}
+
+// Fused plane pass (Z and Y items of each plane through L2).  The sync words
+// (tickets, launch error flag, per-plane counters) are cleared on the stream
+// first; the sticky error word after them is left alone.
+int run_fused(fft3d_plan p, int kind, const ZArgs &z, CLayout ylayout, int forward, cudaStream_t st)
+{
+    FusedArgs f;
+    f.z = z;
+    f.y.src = ylayout;
+    f.y.dst = ylayout;
+    f.y.n0 = p->n0;
+    f.y.n1 = p->n1;
+    f.y.m = p->m;
+    f.y.axis = 1;
+    f.y.inverse = forward ? 0 : 1;
+    const int64_t w = p->gf.per_block;
+    f.yi = (p->m1 + w - 1) / w;
+    f.y.tiles_per_plane = f.yi;
+    f.y.tiles_main = p->n0 * f.yi;
+    f.y.nyq_in_plane = 1;
+    f.n0 = p->n0;
+    f.zi = p->n1 / p->fz_lines;
+#ifndef FFT3D_FUSED_LAG
+#define FFT3D_FUSED_LAG 2
+#endif
+    f.lag = FFT3D_FUSED_LAG;
+    f.n_items = p->n0 * (f.zi + f.yi);
+    f.sync = p->sync;
+    f.spin_limit = p->spin_limit;
+    f.inject_stall = p->inject_stall;
+    f.forward = forward;
+    cudaError_t e = cudaMemsetAsync(p->sync, 0, sizeof(unsigned) * (size_t)(kSyncDone + p->n0), st);
+    if (e != cudaSuccess) return set_err(p, FFT3D_ERR_CUDA, "cudaMemsetAsync", e);
+    return run_pass(p, kind, st,
+                    [&] { return fused_launch_f32((int)p->n1, (int)p->m, f, p->tw1f, p->twz, p->rot, st); });
 }
 
 int check_exec(fft3d_plan p, const void *in, const void *out, bool real_in)
@@ -198,7 +248,18 @@ int forward_pipeline(fft3d_plan p, const void *in, void *out, cudaStream_t st, d
     z.nlines = p->n0 * p->n1;
     z.scale_edge = se;
     z.scale_mid = sm;
-    int rc = run_pass(p, K_R2C_Z, st, [&] {
+    int rc;
+    if (p->fused) {
+        rc = run_fused(p, K_R2C_ZY, z, L, 1, st);
+        if (rc) return rc;
+        if (p->n0 > 1) {
+            int64_t tiles;
+            const ColArgs a = xpass_args(p, L, L, 0, &tiles);
+            rc = run_pass(p, K_R2C_X, st, [&] { return col_launch(p, (int)p->n0, a, tiles, p->tw0, st); });
+        }
+        return rc;
+    }
+    rc = run_pass(p, K_R2C_Z, st, [&] {
         return p->dtype == FFT3D_F32 ? zr2c_launch_f32((int)p->m, z, p->twz, p->rot, st)
                                      : zr2c_launch_f64((int)p->m, z, p->twz, p->rot, st);
     });
@@ -233,12 +294,6 @@ int inverse_pipeline(fft3d_plan p, const void *in, void *out, cudaStream_t st, d
         rc = run_pass(p, K_C2R_X, st, [&] { return col_launch(p, (int)p->n0, a, tiles, p->tw0, st); });
         if (rc) return rc;
     }
-    if (p->n1 > 1) {
-        int64_t tiles;
-        const ColArgs a = ypass_args(p, dst, dst, 1, &tiles);
-        rc = run_pass(p, K_C2R_Y, st, [&] { return col_launch(p, (int)p->n1, a, tiles, p->tw1, st); });
-        if (rc) return rc;
-    }
     ZArgs z;
     z.real = nullptr;
     z.real_out = out;
@@ -247,18 +302,25 @@ int inverse_pipeline(fft3d_plan p, const void *in, void *out, cudaStream_t st, d
     z.nlines = p->n0 * p->n1;
     z.scale_edge = we;
     z.scale_mid = s;
+    if (p->fused) return run_fused(p, K_C2R_YZ, z, dst, 0, st);
+    if (p->n1 > 1) {
+        int64_t tiles;
+        const ColArgs a = ypass_args(p, dst, dst, 1, &tiles);
+        rc = run_pass(p, K_C2R_Y, st, [&] { return col_launch(p, (int)p->n1, a, tiles, p->tw1, st); });
+        if (rc) return rc;
+    }
     return run_pass(p, K_C2R_Z, st, [&] {
         return p->dtype == FFT3D_F32 ? zc2r_launch_f32((int)p->m, z, p->twz, p->rot, st)
                                      : zc2r_launch_f64((int)p->m, z, p->twz, p->rot, st);
     });
 }
 
-cudaError_t gen_line_tables(int dtype, int L, void *dst)
+cudaError_t gen_line_tables(int dtype, int L, int E, void *dst)
 {
-    for (int s = 1; s < line_nstages(L); ++s) {
-        const size_t off = (size_t)line_tw_offset(L, s) * (dtype == FFT3D_F32 ? 8 : 16);
+    for (int s = 1; s < line_nstages(L, E); ++s) {
+        const size_t off = (size_t)line_tw_offset(L, E, s) * (dtype == FFT3D_F32 ? 8 : 16);
         void *o = (char *)dst + off;
-        const int ns = line_ns(L, s), r = line_radix(L, s);
+        const int ns = line_ns(L, E, s), r = line_radix(L, E, s);
         cudaError_t e = dtype == FFT3D_F32 ? twiddle_stage_launch_f32(o, ns, r, 0)
                                            : twiddle_stage_launch_f64(o, ns, r, 0);
         if (e != cudaSuccess) return e;
@@ -308,12 +370,17 @@ int fft3d_plan_create(fft3d_plan *out, int64_t n0, int64_t n1, int64_t n2, int d
         rc = FFT3D_ERR_SIZE;
         goto fail;
     }
+    p->spin_limit = kDefaultSpinLimit;
+    p->fused_ok = f32 && fused_geom_f32((int)n1, (int)p->m, &p->gf, &p->fz_lines) && n1 % p->fz_lines == 0;
+    p->fused = 0;  // opt-in: see fft3d_plan_set_fused
+
     {
-        const size_t s0 = align256((size_t)line_tw_size((int)n0) * p->csize + 16);
-        const size_t s1 = align256((size_t)line_tw_size((int)n1) * p->csize + 16);
-        const size_t sz = align256((size_t)line_tw_size((int)p->m) * p->csize + 16);
+        const size_t s0 = align256((size_t)line_tw_size((int)n0, p->g0.E) * p->csize + 16);
+        const size_t s1 = align256((size_t)line_tw_size((int)n1, p->g1.E) * p->csize + 16);
+        const size_t sz = align256((size_t)line_tw_size((int)p->m, p->gz.E) * p->csize + 16);
         const size_t sr = align256((size_t)p->m * p->csize);
-        e = cudaMalloc(&p->tw, s0 + s1 + sz + sr);
+        const size_t sf = p->fused_ok ? align256((size_t)line_tw_size((int)n1, p->gf.E) * p->csize + 16) : 0;
+        e = cudaMalloc(&p->tw, s0 + s1 + sz + sr + sf);
         if (e != cudaSuccess) {
             rc = FFT3D_ERR_ALLOC;
             goto fail;
@@ -323,11 +390,13 @@ int fft3d_plan_create(fft3d_plan *out, int64_t n0, int64_t n1, int64_t n2, int d
         p->tw1 = base + s0;
         p->twz = base + s0 + s1;
         p->rot = base + s0 + s1 + sz;
-        if ((e = gen_line_tables(dtype, (int)n0, base)) != cudaSuccess ||
-            (e = gen_line_tables(dtype, (int)n1, base + s0)) != cudaSuccess ||
-            (e = gen_line_tables(dtype, (int)p->m, base + s0 + s1)) != cudaSuccess ||
+        p->tw1f = base + s0 + s1 + sz + sr;
+        if ((e = gen_line_tables(dtype, (int)n0, p->g0.E, base)) != cudaSuccess ||
+            (e = gen_line_tables(dtype, (int)n1, p->g1.E, base + s0)) != cudaSuccess ||
+            (e = gen_line_tables(dtype, (int)p->m, p->gz.E, base + s0 + s1)) != cudaSuccess ||
             (e = (f32 ? twiddle_rot_launch_f32 : twiddle_rot_launch_f64)(base + s0 + s1 + sz, (int)n2,
-                                                                         (int)p->m, 0)) != cudaSuccess) {
+                                                                         (int)p->m, 0)) != cudaSuccess ||
+            (p->fused_ok && (e = gen_line_tables(dtype, (int)n1, p->gf.E, base + s0 + s1 + sz + sr)) != cudaSuccess)) {
             rc = FFT3D_ERR_CUDA;
             goto fail;
         }
@@ -335,6 +404,19 @@ int fft3d_plan_create(fft3d_plan *out, int64_t n0, int64_t n1, int64_t n2, int d
         if (e != cudaSuccess) {
             rc = FFT3D_ERR_ALLOC;
             goto fail;
+        }
+        if (p->fused_ok) {
+            const size_t words = (size_t)(kSyncDone + n0 + 1);
+            e = cudaMalloc((void **)&p->sync, words * sizeof(unsigned));
+            if (e != cudaSuccess) {
+                rc = FFT3D_ERR_ALLOC;
+                goto fail;
+            }
+            if ((e = cudaMemset(p->sync, 0, words * sizeof(unsigned))) != cudaSuccess ||
+                (e = fused_prepare_f32((int)n1, (int)p->m)) != cudaSuccess) {
+                rc = FFT3D_ERR_CUDA;
+                goto fail;
+            }
         }
         if ((e = (f32 ? col_prepare_f32 : col_prepare_f64)((int)n0)) != cudaSuccess ||
             (e = (f32 ? col_prepare_f32 : col_prepare_f64)((int)n1)) != cudaSuccess ||
@@ -353,6 +435,7 @@ int fft3d_plan_create(fft3d_plan *out, int64_t n0, int64_t n1, int64_t n2, int d
 fail:
     if (p->tw) cudaFree(p->tw);
     if (p->nyq) cudaFree(p->nyq);
+    if (p->sync) cudaFree(p->sync);
     delete p;
     (void)cudaGetLastError();
     return rc;
@@ -368,8 +451,9 @@ int fft3d_plan_destroy(fft3d_plan p)
     for (auto ev : p->pool) cudaEventDestroy(ev);
     cudaError_t e1 = p->tw ? cudaFree(p->tw) : cudaSuccess;
     cudaError_t e2 = p->nyq ? cudaFree(p->nyq) : cudaSuccess;
+    cudaError_t e3 = p->sync ? cudaFree(p->sync) : cudaSuccess;
     delete p;
-    return (e1 == cudaSuccess && e2 == cudaSuccess) ? FFT3D_OK : FFT3D_ERR_CUDA;
+    return (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess) ? FFT3D_OK : FFT3D_ERR_CUDA;
 }
 
 int fft3d_exec_r2c(fft3d_plan p, const void *in_real, void *out_cplx, void *stream)
@@ -469,6 +553,43 @@ int fft3d_plan_launch_count(fft3d_plan p, int64_t *count)
 {
     if (!p || !count) return FFT3D_ERR_NULL;
     *count = p->launches;
+    return FFT3D_OK;
+}
+
+int fft3d_plan_status(fft3d_plan p, int *device_error)
+{
+    if (!p || !device_error) return FFT3D_ERR_NULL;
+    *device_error = 0;
+    if (!p->sync) return FFT3D_OK;
+    unsigned *sticky = p->sync + kSyncDone + p->n0;
+    unsigned v = 0;
+    cudaError_t e = cudaMemcpy(&v, sticky, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && v) e = cudaMemset(sticky, 0, sizeof(unsigned));
+    if (e != cudaSuccess) return set_err(p, FFT3D_ERR_CUDA, "reading the device error flag", e);
+    *device_error = v ? 1 : 0;
+    return FFT3D_OK;
+}
+
+int fft3d_plan_set_debug(fft3d_plan p, int inject_stall, int64_t spin_limit)
+{
+    if (!p) return FFT3D_ERR_NULL;
+    p->inject_stall = inject_stall ? 1 : 0;
+    p->spin_limit = spin_limit > 0 ? spin_limit : kDefaultSpinLimit;
+    return FFT3D_OK;
+}
+
+int fft3d_plan_info(fft3d_plan p, int *fused_plane_pass)
+{
+    if (!p || !fused_plane_pass) return FFT3D_ERR_NULL;
+    *fused_plane_pass = p->fused;
+    return FFT3D_OK;
+}
+
+int fft3d_plan_set_fused(fft3d_plan p, int enable)
+{
+    if (!p) return FFT3D_ERR_NULL;
+    if (enable && !p->fused_ok) return set_err(p, FFT3D_ERR_SIZE, "no fused plane pass for this shape / dtype");
+    p->fused = enable ? 1 : 0;
     return FFT3D_OK;
 }
 

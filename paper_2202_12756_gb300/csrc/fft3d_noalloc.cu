@@ -86,12 +86,12 @@ cudaError_t scratch_for_current_device(void **out)
     return cudaSuccess;
 }
 
-cudaError_t write_line_tables(bool f32, int L, void *dst, cudaStream_t st)
+cudaError_t write_line_tables(bool f32, int L, int E, void *dst, cudaStream_t st)
 {
-    for (int s = 1; s < line_nstages(L); ++s) {
-        void *o = (char *)dst + (size_t)line_tw_offset(L, s) * (f32 ? 8 : 16);
-        cudaError_t e = f32 ? twiddle_stage_launch_f32(o, line_ns(L, s), line_radix(L, s), st)
-                            : twiddle_stage_launch_f64(o, line_ns(L, s), line_radix(L, s), st);
+    for (int s = 1; s < line_nstages(L, E); ++s) {
+        void *o = (char *)dst + (size_t)line_tw_offset(L, E, s) * (f32 ? 8 : 16);
+        cudaError_t e = f32 ? twiddle_stage_launch_f32(o, line_ns(L, E, s), line_radix(L, E, s), st)
+                            : twiddle_stage_launch_f64(o, line_ns(L, E, s), line_radix(L, E, s), st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -117,9 +117,10 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
         const uintptr_t i0 = (uintptr_t)in_cplx, o0 = (uintptr_t)out_real;
         if (i0 < o0 + ob && o0 < i0 + ib) return FFT3D_ERR_LAYOUT;
     }
-    PassGeom g0, g1;
+    PassGeom g0, g1, gz;
     if (!(f32 ? col_geom_f32((int)n0, &g0) : col_geom_f64((int)n0, &g0)) ||
-        !(f32 ? col_geom_f32((int)n1, &g1) : col_geom_f64((int)n1, &g1)))
+        !(f32 ? col_geom_f32((int)n1, &g1) : col_geom_f64((int)n1, &g1)) ||
+        !(f32 ? z_geom_f32((int)(n2 / 2), &gz) : z_geom_f64((int)(n2 / 2), &gz)))
         return FFT3D_ERR_SIZE;
 
     void *scratch = nullptr;
@@ -132,9 +133,9 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
     void *plane = (char *)scratch + kTableBytes;
 
     cudaError_t e;
-    if ((e = write_line_tables(f32, (int)n0, tw0, st)) != cudaSuccess ||
-        (e = write_line_tables(f32, (int)n1, tw1, st)) != cudaSuccess ||
-        (e = write_line_tables(f32, (int)m, twz, st)) != cudaSuccess ||
+    if ((e = write_line_tables(f32, (int)n0, g0.E, tw0, st)) != cudaSuccess ||
+        (e = write_line_tables(f32, (int)n1, g1.E, tw1, st)) != cudaSuccess ||
+        (e = write_line_tables(f32, (int)m, gz.E, twz, st)) != cudaSuccess ||
         (e = (f32 ? twiddle_rot_launch_f32 : twiddle_rot_launch_f64)(rot, (int)n2, (int)m, st)) != cudaSuccess)
         return FFT3D_ERR_CUDA;
 
@@ -154,6 +155,7 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
         const int64_t tiles = (n1 * m1 + g0.per_block - 1) / g0.per_block;
         a.tiles_main = tiles;
         a.tiles_per_plane = 0;
+        a.nyq_in_plane = 0;
         e = f32 ? col_launch_f32((int)n0, a, tiles, tw0, st) : col_launch_f64((int)n0, a, tiles, tw0, st);
         if (e != cudaSuccess) return FFT3D_ERR_CUDA;
     }
@@ -168,6 +170,7 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
         a.inverse = 1;
         a.tiles_per_plane = (m + g1.per_block - 1) / g1.per_block;
         a.tiles_main = n0 * a.tiles_per_plane;
+        a.nyq_in_plane = 0;
         const int64_t tiles = a.tiles_main + (n0 + g1.per_block - 1) / g1.per_block;
         e = f32 ? col_launch_f32((int)n1, a, tiles, tw1, st) : col_launch_f64((int)n1, a, tiles, tw1, st);
         if (e != cudaSuccess) return FFT3D_ERR_CUDA;

@@ -6,20 +6,49 @@
 
 namespace fft3d {
 
-// Block-size cap of a column pass: 1024 threads while a thread's registers
-// stay within 64 (float, at most 16 elements per thread), else fewer so that
-// the larger register footprint still fits the 64K-register file.
+#ifndef FFT3D_COL_MAXT_F32
+#define FFT3D_COL_MAXT_F32 1024
+#endif
+#ifndef FFT3D_COL_MAXT_F64
+#define FFT3D_COL_MAXT_F64 512
+#endif
+#ifndef FFT3D_Z_THREADS
+#define FFT3D_Z_THREADS 256
+#endif
+
+// Block-size cap of a one-tile-per-block column pass: 1024 threads for float
+// (so a tile row stays one 128-byte segment even at 24 elements per thread,
+// at the price of a few spilled registers there), 512 / 256 for double.
 template <typename R, int L> __host__ __device__ constexpr int col_max_threads()
 {
-    return sizeof(R) == 4 ? (line_E(L) <= 16 ? 1024 : 512) : (line_E(L) <= 16 ? 512 : 256);
+    return sizeof(R) == 4 ? FFT3D_COL_MAXT_F32 : (line_E(L) <= 16 ? FFT3D_COL_MAXT_F64 : 256);
 }
 
+// float columns of 2^k >= 1024 points use the persistent pipelined kernel
+// with 32 elements per thread (radix-32 stages: one exchange at 1024 points);
+// measured on GB300 it is a few percent faster than one tile per block at
+// 1024 points and slower at 512.
+template <typename R, int L> __host__ __device__ constexpr bool col_pipe()
+{
+#ifdef FFT3D_NO_PIPE
+    return false;
+#else
+    return sizeof(R) == 4 && is_pow2(L) && L >= 1024;
+#endif
+}
+
+template <typename R, int L> __host__ __device__ constexpr int col_E() { return col_pipe<R, L>() ? 32 : line_E(L); }
+
 // Columns per tile: one 128-byte segment per row (16 float2 or 8 double2),
-// halved while the block would exceed its thread cap or the tile 200 KB of
-// shared memory.
+// halved while the block would exceed its thread cap or, for the one-tile
+// kernel, the tile 200 KB of shared memory.
 template <typename R, int L> __host__ __device__ constexpr int col_W()
 {
     int w = 128 / (int)sizeof(typename cvec<R>::T);
+    if (col_pipe<R, L>()) {
+        while (w > 1 && w * (L / 32) > 512) w /= 2;
+        return w;
+    }
     while (w > 1 && (w * line_NT(L) > col_max_threads<R, L>() ||
                      (size_t)L * w * sizeof(typename cvec<R>::T) > 200 * 1024))
         w /= 2;
@@ -29,15 +58,19 @@ template <typename R, int L> __host__ __device__ constexpr int col_W()
 // Lines per block of a z pass: about 256 threads, and at least one warp.
 template <int M> __host__ __device__ constexpr int z_LPB()
 {
-    return line_NT(M) >= 256 ? 1 : 256 / line_NT(M);
+    return line_NT(M) >= FFT3D_Z_THREADS ? 1 : FFT3D_Z_THREADS / line_NT(M);
 }
 
 template <typename R, int L> inline void col_geom_t(PassGeom *g)
 {
     constexpr int W = col_W<R, L>();
-    g->threads = W * line_NT(L);
+    constexpr int E = col_E<R, L>();
+    g->threads = W * (L / E);
     g->per_block = W;
+    g->E = E;
+    g->persistent = col_pipe<R, L>() ? 1 : 0;
     g->smem = (size_t)L * W * sizeof(typename cvec<R>::T);
+    if (col_pipe<R, L>()) g->smem += (size_t)split_rows<L>() * W * sizeof(R);
 }
 
 template <typename R, int M> inline void z_geom_t(PassGeom *g)
@@ -45,6 +78,8 @@ template <typename R, int M> inline void z_geom_t(PassGeom *g)
     constexpr int LPB = z_LPB<M>();
     g->threads = LPB * line_NT(M);
     g->per_block = LPB;
+    g->E = line_E(M);
+    g->persistent = 0;
     g->smem = (size_t)LPB * zline_smem_elems<M>() * sizeof(typename cvec<R>::T);
 }
 
@@ -52,19 +87,41 @@ template <typename R, int L> inline cudaError_t col_prepare_t()
 {
     PassGeom g;
     col_geom_t<R, L>(&g);
-    return cudaFuncSetAttribute(colpass_kernel<R, L, col_W<R, L>()>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+    if constexpr (col_pipe<R, L>())
+        return cudaFuncSetAttribute(colpass_pipe_kernel<R, L, col_E<R, L>(), col_W<R, L>()>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+    else
+        return cudaFuncSetAttribute(colpass_kernel<R, L, col_E<R, L>(), col_W<R, L>()>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
 }
 
 template <typename R, int M> inline cudaError_t z_prepare_t()
 {
     PassGeom g;
     z_geom_t<R, M>(&g);
-    cudaError_t e = cudaFuncSetAttribute(zpass_r2c_kernel<R, M, z_LPB<M>()>,
+    cudaError_t e = cudaFuncSetAttribute(zpass_r2c_kernel<R, M, line_E(M), z_LPB<M>()>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(zpass_c2r_kernel<R, M, z_LPB<M>()>,
+    return cudaFuncSetAttribute(zpass_c2r_kernel<R, M, line_E(M), z_LPB<M>()>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+}
+
+// Resident blocks of a persistent kernel on the current device (cached per
+// device for each kernel instantiation).
+template <class K> inline int persistent_grid(K kernel, int threads, size_t smem, int64_t tiles)
+{
+    static int cache[128];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) dev = 0;
+    int per_dev = cache[dev];
+    if (per_dev <= 0) {
+        int sms = 0, nb = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem);
+        per_dev = (sms > 0 ? sms : 1) * (nb > 0 ? nb : 1);
+        cache[dev] = per_dev;
+    }
+    return (int)(tiles < per_dev ? tiles : per_dev);
 }
 
 template <typename R, int L>
@@ -72,8 +129,14 @@ inline cudaError_t col_launch_t(const ColArgs &a, int64_t tiles, const void *tw,
 {
     PassGeom g;
     col_geom_t<R, L>(&g);
-    colpass_kernel<R, L, col_W<R, L>()><<<(unsigned)tiles, g.threads, g.smem, st>>>(
-        a, (const typename cvec<R>::T *)tw);
+    typedef const typename cvec<R>::T *TW;
+    if constexpr (col_pipe<R, L>()) {
+        auto k = colpass_pipe_kernel<R, L, col_E<R, L>(), col_W<R, L>()>;
+        const int grid = persistent_grid(k, g.threads, g.smem, tiles);
+        k<<<grid, g.threads, g.smem, st>>>(a, (TW)tw, tiles);
+    } else {
+        colpass_kernel<R, L, col_E<R, L>(), col_W<R, L>()><<<(unsigned)tiles, g.threads, g.smem, st>>>(a, (TW)tw);
+    }
     return cudaGetLastError();
 }
 
@@ -83,7 +146,7 @@ inline cudaError_t zr2c_launch_t(const ZArgs &a, const void *tw, const void *rot
     PassGeom g;
     z_geom_t<R, M>(&g);
     const int64_t blocks = (a.nlines + g.per_block - 1) / g.per_block;
-    zpass_r2c_kernel<R, M, z_LPB<M>()><<<(unsigned)blocks, g.threads, g.smem, st>>>(
+    zpass_r2c_kernel<R, M, line_E(M), z_LPB<M>()><<<(unsigned)blocks, g.threads, g.smem, st>>>(
         a, (const typename cvec<R>::T *)tw, (const typename cvec<R>::T *)rot);
     return cudaGetLastError();
 }
@@ -94,12 +157,63 @@ inline cudaError_t zc2r_launch_t(const ZArgs &a, const void *tw, const void *rot
     PassGeom g;
     z_geom_t<R, M>(&g);
     const int64_t blocks = (a.nlines + g.per_block - 1) / g.per_block;
-    zpass_c2r_kernel<R, M, z_LPB<M>()><<<(unsigned)blocks, g.threads, g.smem, st>>>(
+    zpass_c2r_kernel<R, M, line_E(M), z_LPB<M>()><<<(unsigned)blocks, g.threads, g.smem, st>>>(
         a, (const typename cvec<R>::T *)tw, (const typename cvec<R>::T *)rot);
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- fused
+// 512 threads per block: Y tiles of W = 512 / (N1 / E1) columns, Z items of
+// 512 / (M / E2) lines; two blocks per SM when a thread holds 16 elements.
+template <int N1, int M> struct FusedShape {
+    static constexpr int T = 512;
+    static constexpr int W = T / (N1 / line_E(N1));
+    static constexpr int LPB = T / (M / line_E(M));
+    static constexpr int MINB = (line_E(N1) <= 16 && line_E(M) <= 16) ? 2 : 1;
+};
+
+template <typename R, int N1, int M> inline void fused_geom_t(PassGeom *g, int *z_lines)
+{
+    typedef FusedShape<N1, M> S;
+    const size_t cs = sizeof(typename cvec<R>::T);
+    const size_t y = (size_t)N1 * S::W * cs;
+    const size_t z = (size_t)S::LPB * zline_smem_elems<M>() * cs;
+    g->threads = S::T;
+    g->per_block = S::W;
+    g->E = line_E(N1);
+    g->persistent = 1;
+    g->smem = y > z ? y : z;
+    *z_lines = S::LPB;
+}
+
+template <typename R, int N1, int M> inline cudaError_t fused_prepare_t()
+{
+    typedef FusedShape<N1, M> S;
+    PassGeom g;
+    int zl;
+    fused_geom_t<R, N1, M>(&g, &zl);
+    return cudaFuncSetAttribute(fused_plane_kernel<R, N1, M, S::W, S::LPB, S::MINB>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+}
+
+template <typename R, int N1, int M>
+inline cudaError_t fused_launch_t(const FusedArgs &a, const void *tw_y, const void *tw_z, const void *rot,
+                                  cudaStream_t st)
+{
+    typedef FusedShape<N1, M> S;
+    typedef const typename cvec<R>::T *TW;
+    PassGeom g;
+    int zl;
+    fused_geom_t<R, N1, M>(&g, &zl);
+    auto k = fused_plane_kernel<R, N1, M, S::W, S::LPB, S::MINB>;
+    const int grid = persistent_grid(k, g.threads, g.smem, a.n_items);
+    k<<<grid, g.threads, g.smem, st>>>(a, (TW)tw_y, (TW)tw_z, (TW)rot);
+    return cudaGetLastError();
+}
+
 }  // namespace fft3d
+
+#define FFT3D_FUSED_SHAPES(X) X(512, 256) X(768, 384) X(1024, 512) X(1536, 768) X(2048, 1024)
 
 #define FFT3D_CASE_COL_GEOM(L) case L: col_geom_t<R, L>(g); return true;
 #define FFT3D_CASE_Z_GEOM(M) case M: z_geom_t<R, M>(g); return true;
@@ -168,4 +282,34 @@ inline cudaError_t zc2r_launch_t(const ZArgs &a, const void *tw, const void *rot
             (typename cvec<R>::T *)out, n, count);                                              \
         return cudaGetLastError();                                                              \
     }                                                                                           \
+    }
+
+#define FFT3D_CASE_FUSED_GEOM(N1, M) \
+    if (n1 == N1 && m == M) {         \
+        fused_geom_t<R, N1, M>(g, zl); \
+        return true;                   \
+    }
+#define FFT3D_CASE_FUSED_PREP(N1, M) \
+    if (n1 == N1 && m == M) return fused_prepare_t<R, N1, M>();
+#define FFT3D_CASE_FUSED_LAUNCH(N1, M) \
+    if (n1 == N1 && m == M) return fused_launch_t<R, N1, M>(a, tw_y, tw_z, rot, st);
+
+#define FFT3D_DEFINE_FUSED(SUF)                                                                   \
+    namespace fft3d {                                                                             \
+    bool fused_geom_##SUF(int n1, int m, PassGeom *g, int *zl)                                    \
+    {                                                                                             \
+        FFT3D_FUSED_SHAPES(FFT3D_CASE_FUSED_GEOM)                                                 \
+        return false;                                                                             \
+    }                                                                                             \
+    cudaError_t fused_prepare_##SUF(int n1, int m)                                                \
+    {                                                                                             \
+        FFT3D_FUSED_SHAPES(FFT3D_CASE_FUSED_PREP)                                                 \
+        return cudaErrorInvalidValue;                                                             \
+    }                                                                                             \
+    cudaError_t fused_launch_##SUF(int n1, int m, const FusedArgs &a, const void *tw_y,          \
+                                   const void *tw_z, const void *rot, cudaStream_t st)            \
+    {                                                                                             \
+        FFT3D_FUSED_SHAPES(FFT3D_CASE_FUSED_LAUNCH)                                               \
+        return cudaErrorInvalidValue;                                                             \
+    }                                                                                             \
     }

@@ -4,7 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "pass_kernels.cuh"
+#include "fused_kernel.cuh"
 
 namespace fft3d {
 
@@ -20,6 +20,8 @@ namespace fft3d {
 struct PassGeom {
     int threads;      // block size
     int per_block;    // columns (colpass) or lines (zpass) per block
+    int E;            // elements per thread (fixes the twiddle-table layout)
+    int persistent;   // 1: grid-stride persistent kernel
     size_t smem;      // dynamic shared memory bytes
 };
 
@@ -43,5 +45,15 @@ struct PassGeom {
 
 FFT3D_DECLARE_LAUNCHERS(f32, float)
 FFT3D_DECLARE_LAUNCHERS(f64, double)
+
+// Fused plane pass (float only): available for (N1, M) in
+// {(512, 256), (768, 384), (1024, 512), (1536, 768), (2048, 1024)}.
+// geom->per_block = W (columns per Y tile), geom->E = elements per thread of
+// the axis-1 transform (twiddle layout), geom->threads, geom->smem;
+// z_lines = lines per Z item.
+bool fused_geom_f32(int n1, int m, PassGeom *geom, int *z_lines);
+cudaError_t fused_prepare_f32(int n1, int m);
+cudaError_t fused_launch_f32(int n1, int m, const FusedArgs &a, const void *tw_y, const void *tw_z,
+                             const void *rot, cudaStream_t st);
 
 }  // namespace fft3d

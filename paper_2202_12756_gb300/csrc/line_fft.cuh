@@ -165,24 +165,73 @@ template <typename C> struct Dft<16, C> {
     }
 };
 
-// One Stockham stage s of a length-L line.  Thread j holds v[i] = x[j + i NT].
-// Butterfly b = j + q NT (q < E / R) combines x[b + m L/R], m < R, which are
-// v[q + m E/R]; with k = b mod Ns it applies W_{Ns R}^{m k}, a radix-R DFT,
-// and writes y[(b / Ns) Ns R + k + m Ns].  Non-final stages write through the
-// exchange `ex` and read back x'[j + i NT]; the final stage's output slots
-// coincide with its input slots, so it stays in registers (natural order).
-template <typename R, int L, int S, class Ex>
-__device__ __forceinline__ void line_stage(typename cvec<R>::T *v, int j,
-                                           const typename cvec<R>::T *__restrict__ tw, Ex &ex)
+// z * (cr + i ci) for a compile-time constant root of unity
+template <typename C> __device__ __forceinline__ C cmulk(C z, double cr, double ci)
+{
+    typedef decltype(C::x) R;
+    return cmake<C>(z.x * R(cr) - z.y * R(ci), z.x * R(ci) + z.y * R(cr));
+}
+
+// cos(pi/16), sin(pi/16), cos(3 pi/16), sin(3 pi/16)
+#define FFT3D_C16 0.980785280403230449126182236134239037
+#define FFT3D_S16 0.195090322016128267848284868477022240
+#define FFT3D_C316 0.831469612302545237078788377617905756
+#define FFT3D_S316 0.555570233019602224742830813948532874
+
+template <typename C> struct Dft<32, C> {
+    // radix 2 x 16: y[k] = E[k] + W32^k O[k], y[k + 16] = E[k] - W32^k O[k]
+    __device__ __forceinline__ static void run(C *a)
+    {
+        C e[16], o[16];
+#pragma unroll
+        for (int n = 0; n < 16; ++n) {
+            e[n] = a[2 * n];
+            o[n] = a[2 * n + 1];
+        }
+        Dft<16, C>::run(e);
+        Dft<16, C>::run(o);
+        // W32^k = exp(-2 pi i k / 32), k = 1..15
+        o[1] = cmulk(o[1], FFT3D_C16, -FFT3D_S16);
+        o[2] = cmulk(o[2], FFT3D_C8, -FFT3D_S8);
+        o[3] = cmulk(o[3], FFT3D_C316, -FFT3D_S316);
+        o[4] = w8_1(o[4]);
+        o[5] = cmulk(o[5], FFT3D_S316, -FFT3D_C316);
+        o[6] = cmulk(o[6], FFT3D_S8, -FFT3D_C8);
+        o[7] = cmulk(o[7], FFT3D_S16, -FFT3D_C16);
+        o[8] = cmul_mi(o[8]);
+        o[9] = cmulk(o[9], -FFT3D_S16, -FFT3D_C16);
+        o[10] = cmulk(o[10], -FFT3D_S8, -FFT3D_C8);
+        o[11] = cmulk(o[11], -FFT3D_S316, -FFT3D_C316);
+        o[12] = w8_3(o[12]);
+        o[13] = cmulk(o[13], -FFT3D_C316, -FFT3D_S316);
+        o[14] = cmulk(o[14], -FFT3D_C8, -FFT3D_S8);
+        o[15] = cmulk(o[15], -FFT3D_C16, -FFT3D_S16);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            a[k] = cadd(e[k], o[k]);
+            a[k + 16] = csub(e[k], o[k]);
+        }
+    }
+};
+
+// Stockham stage s of a length-L line, E elements per thread.  Thread j holds
+// v[i] = x[j + i NT].  Butterfly b = j + q NT (q < E / R) combines
+// x[b + m L/R], m < R, which are v[q + m E/R]; with k = b mod Ns it applies
+// W_{Ns R}^{m k} and a radix-R DFT.  Its outputs belong at
+// y[(b / Ns) Ns R + k + m Ns]; they are left in the input slots and the
+// exchange (for every stage but the last) moves them to their owners.  The
+// last stage's output slots coincide with its input slots (natural order).
+template <typename R, int L, int E, int S>
+__device__ __forceinline__ void line_stage_compute(typename cvec<R>::T *v, int j,
+                                                   const typename cvec<R>::T *__restrict__ tw)
 {
     typedef typename cvec<R>::T C;
-    constexpr int E = line_E(L);
     constexpr int NT = L / E;
-    constexpr int RS = line_radix(L, S);
-    constexpr int NS = line_ns(L, S);
+    constexpr int RS = line_radix(L, E, S);
+    constexpr int NS = line_ns(L, E, S);
     constexpr int Q = E / RS;
-    constexpr bool LAST = (S == line_nstages(L) - 1);
-    constexpr int TWO = line_tw_offset(L, S);
+    constexpr int TWO = line_tw_offset(L, E, S);
+    static_assert(E % RS == 0, "radix must divide the elements per thread");
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int b = j + q * NT;
@@ -195,39 +244,93 @@ __device__ __forceinline__ void line_stage(typename cvec<R>::T *v, int j,
             for (int m = 1; m < RS; ++m) t[m] = cmul(t[m], __ldg(tw + TWO + (m - 1) * NS + k));
         }
         Dft<RS, C>::run(t);
-        if (LAST) {
 #pragma unroll
-            for (int m = 0; m < RS; ++m) v[q + m * Q] = t[m];
-        } else {
-            const int base = (b / NS) * NS * RS + k;
-#pragma unroll
-            for (int m = 0; m < RS; ++m) ex.put(base + m * NS, t[m]);
-        }
+        for (int m = 0; m < RS; ++m) v[q + m * Q] = t[m];
     }
-    if (!LAST) {
+}
+
+// destination index of slot q + m Q after stage S
+template <int L, int E, int S> __device__ __forceinline__ int line_stage_dest(int j, int q, int m)
+{
+    constexpr int NT = L / E;
+    constexpr int RS = line_radix(L, E, S);
+    constexpr int NS = line_ns(L, E, S);
+    const int b = j + q * NT;
+    return (b / NS) * NS * RS + (b % NS) + m * NS;
+}
+
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+// Exchange after stage S: every slot's value goes to the thread that owns
+// its destination index.  `hook` runs once, right after the first barrier
+// (when every thread's earlier shared-memory reads have completed).
+template <typename R, int L, int E, int S, class Ex, class Hook>
+__device__ __forceinline__ void line_exchange(typename cvec<R>::T *v, int j, Ex &ex, const Hook &hook)
+{
+    constexpr int NT = L / E;
+    constexpr int RS = line_radix(L, E, S);
+    constexpr int Q = E / RS;
+    if constexpr (Ex::kSplit) {
+        // real parts, then imaginary parts, through a buffer of half the size
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int m = 0; m < RS; ++m) ex.put_real(line_stage_dest<L, E, S>(j, q, m), v[q + m * Q].x);
         ex.sync();
+        hook();
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i].x = ex.get_real(j + i * NT);
+        ex.sync();
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int m = 0; m < RS; ++m) ex.put_real(line_stage_dest<L, E, S>(j, q, m), v[q + m * Q].y);
+        ex.sync();
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i].y = ex.get_real(j + i * NT);
+        ex.sync();
+    } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int m = 0; m < RS; ++m) ex.put(line_stage_dest<L, E, S>(j, q, m), v[q + m * Q]);
+        ex.sync();
+        hook();
 #pragma unroll
         for (int i = 0; i < E; ++i) v[i] = ex.get(j + i * NT);
         ex.sync();
     }
 }
 
-template <typename R, int L, int S, class Ex>
+template <typename R, int L, int E, int S, class Ex, class Hook>
 __device__ __forceinline__ void line_stages_from(typename cvec<R>::T *v, int j,
-                                                 const typename cvec<R>::T *__restrict__ tw, Ex &ex)
+                                                 const typename cvec<R>::T *__restrict__ tw, Ex &ex,
+                                                 const Hook &hook)
 {
-    if constexpr (S < line_nstages(L)) {
-        line_stage<R, L, S>(v, j, tw, ex);
-        line_stages_from<R, L, S + 1>(v, j, tw, ex);
+    if constexpr (S < line_nstages(L, E)) {
+        line_stage_compute<R, L, E, S>(v, j, tw);
+        if constexpr (S + 1 < line_nstages(L, E)) {
+            if constexpr (S == 0) line_exchange<R, L, E, S>(v, j, ex, hook);
+            else line_exchange<R, L, E, S>(v, j, ex, NoHook());
+        } else if constexpr (S == 0) {
+            hook();
+        }
+        line_stages_from<R, L, E, S + 1>(v, j, tw, ex, hook);
     }
 }
 
 // Forward FFT of a line held as v[i] = x[j + i NT]; result in the same slots.
-template <typename R, int L, class Ex>
+// `hook` runs once after the first exchange barrier (or after the only stage).
+template <typename R, int L, int E, class Ex, class Hook = NoHook>
 __device__ __forceinline__ void line_fft(typename cvec<R>::T *v, int j,
-                                         const typename cvec<R>::T *__restrict__ tw, Ex &ex)
+                                         const typename cvec<R>::T *__restrict__ tw, Ex &ex,
+                                         const Hook &hook = Hook())
 {
-    line_stages_from<R, L, 0>(v, j, tw, ex);
+    static_assert(line_plan_valid(L, E), "invalid line plan");
+    if constexpr (line_nstages(L, E) == 0) hook();
+    line_stages_from<R, L, E, 0>(v, j, tw, ex, hook);
 }
 
 }  // namespace fft3d

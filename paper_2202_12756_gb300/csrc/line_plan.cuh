@@ -6,8 +6,9 @@
 // sequence R_0 .. R_{S-1} (product L, every R_s dividing E) is run as a
 // Stockham autosort FFT: stage s combines R_s sub-transforms of length
 // Ns = R_0 * .. * R_{s-1}, so the output comes out in natural order with no
-// bit reversal.  Power-of-two lengths use radix 16 (then one smaller radix);
-// 3 * 2^k lengths use one radix-3 stage followed by radix 8 (then smaller).
+// bit reversal.  Power-of-two lengths use radix min(E, 32) (then one smaller
+// radix); 3 * 2^k lengths use one radix-3 stage followed by radix 8 (then
+// smaller).
 #pragma once
 
 #include <stdint.h>
@@ -21,7 +22,7 @@ __host__ __device__ constexpr bool line_supported(int L)
     return L >= 1 && L <= 2048 && (is_pow2(L) || (L % 3 == 0 && is_pow2(L / 3) && L / 3 <= 512));
 }
 
-// elements per thread
+// default elements per thread: 16 for powers of two, 24 for 3 * 2^k
 __host__ __device__ constexpr int line_E(int L)
 {
     return is_pow2(L) ? (L < 16 ? L : 16) : 3 * ((L / 3) < 8 ? (L / 3) : 8);
@@ -29,14 +30,20 @@ __host__ __device__ constexpr int line_E(int L)
 
 __host__ __device__ constexpr int line_NT(int L) { return L / line_E(L); }
 
-__host__ __device__ constexpr int line_nstages(int L)
+// largest power-of-two radix used with E elements per thread
+__host__ __device__ constexpr int line_cap(int L, int E)
+{
+    return is_pow2(L) ? (E < 32 ? E : 32) : 8;
+}
+
+__host__ __device__ constexpr int line_nstages(int L, int E)
 {
     int rem = L, s = 0;
     if (!is_pow2(L)) {
         rem /= 3;
         s = 1;
     }
-    const int cap = is_pow2(L) ? 16 : 8;
+    const int cap = line_cap(L, E);
     while (rem > 1) {
         const int r = rem < cap ? rem : cap;
         rem /= r;
@@ -45,7 +52,7 @@ __host__ __device__ constexpr int line_nstages(int L)
     return s;
 }
 
-__host__ __device__ constexpr int line_radix(int L, int s)
+__host__ __device__ constexpr int line_radix(int L, int E, int s)
 {
     int rem = L, i = 0;
     if (!is_pow2(L)) {
@@ -53,7 +60,7 @@ __host__ __device__ constexpr int line_radix(int L, int s)
         rem /= 3;
         i = 1;
     }
-    const int cap = is_pow2(L) ? 16 : 8;
+    const int cap = line_cap(L, E);
     while (rem > 1) {
         const int r = rem < cap ? rem : cap;
         if (i == s) return r;
@@ -64,22 +71,31 @@ __host__ __device__ constexpr int line_radix(int L, int s)
 }
 
 // Ns of stage s: product of the radices before it
-__host__ __device__ constexpr int line_ns(int L, int s)
+__host__ __device__ constexpr int line_ns(int L, int E, int s)
 {
     int p = 1;
-    for (int i = 0; i < s; ++i) p *= line_radix(L, i);
+    for (int i = 0; i < s; ++i) p *= line_radix(L, E, i);
     return p;
 }
 
 // Stage s > 0 reads twiddles W_{Ns R}^{m k} (m = 1..R-1, k < Ns) from
 // table[offset(s) + (m - 1) * Ns + k]; stage 0 needs none (all k = 0).
-__host__ __device__ constexpr int line_tw_offset(int L, int s)
+__host__ __device__ constexpr int line_tw_offset(int L, int E, int s)
 {
     int o = 0;
-    for (int i = 1; i < s; ++i) o += (line_radix(L, i) - 1) * line_ns(L, i);
+    for (int i = 1; i < s; ++i) o += (line_radix(L, E, i) - 1) * line_ns(L, E, i);
     return o;
 }
 
-__host__ __device__ constexpr int line_tw_size(int L) { return line_tw_offset(L, line_nstages(L)); }
+__host__ __device__ constexpr int line_tw_size(int L, int E) { return line_tw_offset(L, E, line_nstages(L, E)); }
+
+// every radix divides E (so each thread runs whole butterflies)
+__host__ __device__ constexpr bool line_plan_valid(int L, int E)
+{
+    if (E < 1 || L % E != 0) return false;
+    for (int s = 0; s < line_nstages(L, E); ++s)
+        if (E % line_radix(L, E, s) != 0) return false;
+    return true;
+}
 
 }  // namespace fft3d

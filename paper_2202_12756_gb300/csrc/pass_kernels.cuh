@@ -45,6 +45,7 @@ struct ColArgs {
     int inverse;              // 1: exp(+...) via conj in / conj out
     int64_t tiles_main;       // tiles of the main column set
     int64_t tiles_per_plane;  // y-pass: main tiles per k0 plane
+    int nyq_in_plane;         // y-pass: tiles cover k2 = 0..M of one plane (last one ragged)
 };
 
 template <typename C>
@@ -68,6 +69,7 @@ __device__ __forceinline__ void layout_column(const CLayout &l, int64_t n1, int6
 // W * sizeof(complex) = 128 bytes, each half/quarter-warp access is one row:
 // conflict-free without padding.
 template <typename C, int W> struct ColEx {
+    static constexpr bool kSplit = false;
     C *sm;
     int c;
     __device__ __forceinline__ void put(int row, C v) { sm[row * W + c] = v; }
@@ -75,19 +77,12 @@ template <typename C, int W> struct ColEx {
     __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 
-template <typename R, int L, int W>
-__global__ void __launch_bounds__(W *(L / line_E(L)))
-colpass_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw)
+// Which column lane c of tile t owns, and where it lives in the source and
+// destination layouts.  Returns false for lanes past the last column.
+template <typename C, int W>
+__device__ __forceinline__ bool col_decode(const ColArgs &a, int64_t t, int c, C *&sp, int64_t &ss, C *&dp,
+                                           int64_t &ds)
 {
-    typedef typename cvec<R>::T C;
-    constexpr int E = line_E(L);
-    constexpr int NT = L / E;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int c = threadIdx.x % W;
-    const int j = threadIdx.x / W;
-    const int64_t t = blockIdx.x;
-
-    // which column this lane owns
     int64_t k0 = 0, k1 = 0, k2 = 0;
     bool valid;
     if (a.axis == 0) {
@@ -95,6 +90,10 @@ colpass_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw)
         valid = f < a.n1 * (a.m + 1);
         k1 = f / (a.m + 1);
         k2 = f - k1 * (a.m + 1);
+    } else if (a.nyq_in_plane) {
+        k0 = t / a.tiles_per_plane;
+        k2 = (t - k0 * a.tiles_per_plane) * W + c;
+        valid = k2 <= a.m;
     } else if (t < a.tiles_main) {
         k0 = t / a.tiles_per_plane;
         k2 = (t - k0 * a.tiles_per_plane) * W + c;
@@ -104,21 +103,54 @@ colpass_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw)
         k2 = a.m;
         valid = k0 < a.n0;
     }
-    C *sp = nullptr, *dp = nullptr;
-    int64_t ss = 0, ds = 0;
     if (valid) {
         layout_column<C>(a.src, a.n1, a.m, a.axis, k0, k1, k2, sp, ss);
         layout_column<C>(a.dst, a.n1, a.m, a.axis, k0, k1, k2, dp, ds);
     }
+    return valid;
+}
+
+// Split exchange of a column tile: real parts, then imaginary parts, through
+// an [L][W] buffer of reals (half the size of a complex one).  One padding
+// row every 32 rows keeps the stride-32-row writes of a radix-32 stage free of
+// bank conflicts (W reals = 64 bytes per row).
+template <typename R, int W> struct ColSplitEx {
+    static constexpr bool kSplit = true;
+    R *sm;
+    int c;
+    __device__ __forceinline__ int idx(int row) const { return (row + (row >> 5)) * W + c; }
+    __device__ __forceinline__ void put_real(int row, R v) { sm[idx(row)] = v; }
+    __device__ __forceinline__ R get_real(int row) const { return sm[idx(row)]; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+
+// Loads that bypass L1: a tile written earlier in the same kernel by another
+// block is read from L2, never from a stale L1 line.
+template <typename C> __device__ __forceinline__ C load_cg(const C *p) { return __ldcg(p); }
+
+// One column tile (W columns x L rows) with the block's threads; the tile is
+// loaded straight into registers.  CG selects L2-only loads.
+template <typename R, int L, int E, int W, bool CG>
+__device__ __forceinline__ void col_tile(const ColArgs &a, int64_t tile, unsigned char *smem,
+                                         const typename cvec<R>::T *__restrict__ tw)
+{
+    typedef typename cvec<R>::T C;
+    constexpr int NT = L / E;
+    const int c = threadIdx.x % W;
+    const int j = threadIdx.x / W;
+    C *sp = nullptr, *dp = nullptr;
+    int64_t ss = 0, ds = 0;
+    const bool valid = col_decode<C, W>(a, tile, c, sp, ss, dp, ds);
 
     C v[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) {
-        v[i] = valid ? sp[(int64_t)(j + i * NT) * ss] : cmake<C>(R(0), R(0));
+        if (valid) v[i] = CG ? load_cg(sp + (int64_t)(j + i * NT) * ss) : sp[(int64_t)(j + i * NT) * ss];
+        else v[i] = cmake<C>(R(0), R(0));
         if (a.inverse) v[i].y = -v[i].y;
     }
-    ColEx<C, W> ex{(C *)smem_raw, c};
-    line_fft<R, L>(v, j, tw, ex);
+    ColEx<C, W> ex{(C *)smem, c};
+    line_fft<R, L, E>(v, j, tw, ex);
     if (valid) {
 #pragma unroll
         for (int i = 0; i < E; ++i) {
@@ -127,6 +159,106 @@ colpass_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw)
             dp[(int64_t)(j + i * NT) * ds] = o;
         }
     }
+}
+
+// One tile per block.
+template <typename R, int L, int E, int W>
+__global__ void __launch_bounds__(W *(L / E))
+colpass_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    col_tile<R, L, E, W, false>(a, blockIdx.x, smem_raw, tw);
+}
+
+template <int L> __host__ __device__ constexpr int split_rows() { return L + (L >> 5) + 1; }
+
+__device__ __forceinline__ void cp_async_8(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Persistent, software-pipelined column pass.  Each block walks the tiles
+// t = blockIdx.x, blockIdx.x + gridDim.x, ...  While a tile is transformed in
+// registers, the next tile is already streaming from HBM into a shared-memory
+// staging buffer with asynchronous copies (cp.async).  Every thread stages
+// exactly the elements it will later own (rows j + i NT of its column), so a
+// thread only waits for its own copies; it issues the next tile's copies into
+// its slots after the first exchange barrier, when its reads of them have
+// completed.  The stage exchange uses a separate split (real / imaginary)
+// buffer.  Shared memory: L W complex (staging) + (L + L/32 + 1) W reals.
+template <typename R, int L, int E, int W>
+__global__ void __launch_bounds__(W *(L / E), (W * (L / E) >= 512 ? 1 : 512 / (W * (L / E))))
+colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64_t ntiles)
+{
+    typedef typename cvec<R>::T C;
+    constexpr int NT = L / E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *stage = (C *)smem_raw;
+    ColSplitEx<R, W> ex{(R *)(stage + L * W), 0};
+    const int c = threadIdx.x % W;
+    const int j = threadIdx.x / W;
+    ex.c = c;
+
+    auto prefetch = [&](const C *sp, int64_t ss) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            C *dst = stage + (j + i * NT) * W + c;
+            const C *src = sp + (int64_t)(j + i * NT) * ss;
+            if (sizeof(C) == 8) cp_async_8(dst, src);
+            else cp_async_16(dst, src);
+        }
+    };
+
+    int64_t t = blockIdx.x;
+    C *sp = nullptr, *dp = nullptr;
+    int64_t ss = 0, ds = 0;
+    bool valid = t < ntiles && col_decode<C, W>(a, t, c, sp, ss, dp, ds);
+    if (valid) prefetch(sp, ss);
+    cp_async_commit();
+    while (t < ntiles) {
+        const int64_t tn = t + gridDim.x;
+        C *spn = nullptr, *dpn = nullptr;
+        int64_t ssn = 0, dsn = 0;
+        const bool validn = tn < ntiles && col_decode<C, W>(a, tn, c, spn, ssn, dpn, dsn);
+
+        cp_async_wait_all();  // this thread's copies of tile t have landed
+        C v[E];
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            v[i] = valid ? stage[(j + i * NT) * W + c] : cmake<C>(R(0), R(0));
+            if (a.inverse) v[i].y = -v[i].y;
+        }
+        // Stage the next tile into the same slots once these reads are
+        // complete, i.e. after the first exchange barrier.
+        auto next = [&]() {
+            if (validn) prefetch(spn, ssn);
+            cp_async_commit();
+        };
+        line_fft<R, L, E>(v, j, tw, ex, next);
+        if (valid) {
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                C o = v[i];
+                if (a.inverse) o.y = -o.y;
+                dp[(int64_t)(j + i * NT) * ds] = o;
+            }
+        }
+        t = tn;
+        valid = validn;
+        sp = spn;
+        ss = ssn;
+        dp = dpn;
+        ds = dsn;
+    }
+    cp_async_wait_all();
 }
 
 // ------------------------------------------------------------ z pass
@@ -143,6 +275,7 @@ struct ZArgs {
 // Per-line shared-memory exchange with one padding slot every 16 elements,
 // which makes the stride-16 writes of a radix-16 first stage conflict-free.
 template <typename C, int NT> struct LineEx {
+    static constexpr bool kSplit = false;
     C *sm;
     __device__ __forceinline__ static int pad(int i) { return i + (i >> 4); }
     __device__ __forceinline__ void put(int i, C v) { sm[pad(i)] = v; }
@@ -156,27 +289,27 @@ template <typename C, int NT> struct LineEx {
 
 template <int M> __host__ __device__ constexpr int zline_smem_elems() { return (M + 1) + ((M + 1) >> 4) + 1; }
 
-template <typename R, int M, int LPB>
-__global__ void __launch_bounds__(LPB *(M / line_E(M)))
-zpass_r2c_kernel(ZArgs a, const typename cvec<R>::T *__restrict__ tw,
-                 const typename cvec<R>::T *__restrict__ rot)
+// LPB lines starting at line0, NT = M / E threads per line.  R2C: load the
+// real line as M complex pairs, M-point FFT, Hermitian post-process.
+template <typename R, int M, int E, int LPB>
+__device__ __forceinline__ void zr2c_lines(const ZArgs &a, int64_t line0, unsigned char *smem,
+                                           const typename cvec<R>::T *__restrict__ tw,
+                                           const typename cvec<R>::T *__restrict__ rot)
 {
     typedef typename cvec<R>::T C;
-    constexpr int E = line_E(M);
     constexpr int NT = M / E;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lt = threadIdx.x / NT;
     const int j = threadIdx.x % NT;
-    const int64_t line = (int64_t)blockIdx.x * LPB + lt;
+    const int64_t line = line0 + lt;
     const bool active = line < a.nlines;
-    LineEx<C, NT> ex{(C *)smem_raw + lt * zline_smem_elems<M>()};
+    LineEx<C, NT> ex{(C *)smem + lt * zline_smem_elems<M>()};
 
     const C *in = (const C *)((const R *)a.real + (active ? line : 0) * a.real_pitch);
     C v[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) v[i] = active ? in[j + i * NT] : cmake<C>(R(0), R(0));
 
-    line_fft<R, M>(v, j, tw, ex);
+    line_fft<R, M, E>(v, j, tw, ex);
 
     // Hermitian post-process: needs Z[k] and Z[M - k] together
 #pragma unroll
@@ -189,8 +322,8 @@ zpass_r2c_kernel(ZArgs a, const typename cvec<R>::T *__restrict__ tw,
         const int k = j + i * NT;
         const C z = ex.get(k);
         const C zc = cconj(ex.get(k == 0 ? 0 : M - k));
-        const C s = cadd(z, zc);           // 2 E[k]
-        const C d = cmul(__ldg(rot + k), csub(z, zc));  // 2i W^k O[k]
+        const C s = cadd(z, zc);                         // 2 E[k]
+        const C d = cmul(__ldg(rot + k), csub(z, zc));   // 2i W^k O[k]
         // X[k] = (s - i d) / 2
         const R f = R(0.5) * (k == 0 ? se : sm);
         if (active) out[k] = cmake<C>(f * (s.x + d.y), f * (s.y - d.x));
@@ -201,20 +334,20 @@ zpass_r2c_kernel(ZArgs a, const typename cvec<R>::T *__restrict__ tw,
     }
 }
 
-template <typename R, int M, int LPB>
-__global__ void __launch_bounds__(LPB *(M / line_E(M)))
-zpass_c2r_kernel(ZArgs a, const typename cvec<R>::T *__restrict__ tw,
-                 const typename cvec<R>::T *__restrict__ rot)
+// C2R of LPB lines: Hermitian pre-process, M-point inverse FFT, unpack into
+// 2M reals with the output scale.  CG selects L2-only loads of the spectrum.
+template <typename R, int M, int E, int LPB, bool CG>
+__device__ __forceinline__ void zc2r_lines(const ZArgs &a, int64_t line0, unsigned char *smem,
+                                           const typename cvec<R>::T *__restrict__ tw,
+                                           const typename cvec<R>::T *__restrict__ rot)
 {
     typedef typename cvec<R>::T C;
-    constexpr int E = line_E(M);
     constexpr int NT = M / E;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lt = threadIdx.x / NT;
     const int j = threadIdx.x % NT;
-    const int64_t line = (int64_t)blockIdx.x * LPB + lt;
+    const int64_t line = line0 + lt;
     const bool active = line < a.nlines;
-    LineEx<C, NT> ex{(C *)smem_raw + lt * zline_smem_elems<M>()};
+    LineEx<C, NT> ex{(C *)smem + lt * zline_smem_elems<M>()};
 
     const int64_t l = active ? line : 0;
     const C *src;
@@ -228,10 +361,11 @@ zpass_c2r_kernel(ZArgs a, const typename cvec<R>::T *__restrict__ tw,
     }
     C v[E];
 #pragma unroll
-    for (int i = 0; i < E; ++i) v[i] = active ? src[j + i * NT] : cmake<C>(R(0), R(0));
+    for (int i = 0; i < E; ++i)
+        v[i] = active ? (CG ? load_cg(src + j + i * NT) : src[j + i * NT]) : cmake<C>(R(0), R(0));
 #pragma unroll
     for (int i = 0; i < E; ++i) ex.put(j + i * NT, v[i]);
-    if (j == 0) ex.put(M, active ? *nyq : cmake<C>(R(0), R(0)));
+    if (j == 0) ex.put(M, active ? (CG ? load_cg(nyq) : *nyq) : cmake<C>(R(0), R(0)));
     ex.sync();
 
     const R we = R(a.scale_edge);
@@ -246,14 +380,14 @@ zpass_c2r_kernel(ZArgs a, const typename cvec<R>::T *__restrict__ tw,
             y = cmake<C>(we * y.x, R(0));
         }
         const C yc = cconj(y);
-        const C e = cadd(x, yc);                      // E[k] (times 2)
+        const C e = cadd(x, yc);                         // E[k] (times 2)
         const C o = cmulc(csub(x, yc), __ldg(rot + k));  // O[k] (times 2)
         // Z = E + i O, kept conjugated for the inverse transform
         v[i] = cmake<C>(e.x - o.y, -(e.y + o.x));
     }
     ex.sync();
 
-    line_fft<R, M>(v, j, tw, ex);
+    line_fft<R, M, E>(v, j, tw, ex);
 
     const R s = R(a.scale_mid);
     C *out = (C *)((R *)a.real_out + l * a.real_pitch);
@@ -261,6 +395,24 @@ zpass_c2r_kernel(ZArgs a, const typename cvec<R>::T *__restrict__ tw,
 #pragma unroll
         for (int i = 0; i < E; ++i) out[j + i * NT] = cmake<C>(s * v[i].x, -s * v[i].y);
     }
+}
+
+template <typename R, int M, int E, int LPB>
+__global__ void __launch_bounds__(LPB *(M / E))
+zpass_r2c_kernel(ZArgs a, const typename cvec<R>::T *__restrict__ tw,
+                 const typename cvec<R>::T *__restrict__ rot)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    zr2c_lines<R, M, E, LPB>(a, (int64_t)blockIdx.x * LPB, smem_raw, tw, rot);
+}
+
+template <typename R, int M, int E, int LPB>
+__global__ void __launch_bounds__(LPB *(M / E))
+zpass_c2r_kernel(ZArgs a, const typename cvec<R>::T *__restrict__ tw,
+                 const typename cvec<R>::T *__restrict__ rot)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    zc2r_lines<R, M, E, LPB, false>(a, (int64_t)blockIdx.x * LPB, smem_raw, tw, rot);
 }
 
 // ------------------------------------------------------------ twiddles

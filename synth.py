@@ -121,3 +121,35 @@ def turbulence_spectrum_device(n0, n1, n2, seed, device, kmin=1.0, kmax=None, sl
         phase = torch.rand((n1, m1), generator=gen, dtype=torch.float64, device=device) * (2.0 * np.pi)
         out[i] = torch.polar(amp, phase)
     return out
+
+
+def uniform_field_device(shape, seed, device, dtype=None, out=None):
+    """iid uniform[-1, 1) field drawn on a CUDA device with torch's seeded
+    generator (for grids too large to draw and ship from the host); `out`
+    may be a strided view (e.g. the real part of a padded buffer)."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    t = torch.empty(tuple(shape), dtype=dtype or torch.float64, device=device) if out is None else out
+    t.uniform_(-1.0, 1.0, generator=gen)
+    return t
+
+
+def plane_waves_device(shape, kvecs, device, dtype=None, out=None):
+    """sum over k of cos(2 pi (k0 j0/N0 + k1 j1/N1 + k2 j2/N2)) on a CUDA
+    device, phases reduced mod N on integers before scaling."""
+    import torch
+    n0, n1, n2 = shape
+    dtype = dtype or torch.float64
+    out = torch.zeros(tuple(shape), dtype=dtype, device=device) if out is None else out
+    j0 = torch.arange(n0, dtype=torch.int64, device=device)
+    j1 = torch.arange(n1, dtype=torch.int64, device=device)
+    j2 = torch.arange(n2, dtype=torch.int64, device=device)
+    for k0, k1, k2 in kvecs:
+        e0 = torch.exp(2j * np.pi * ((int(k0) * j0) % n0).to(torch.float64) / n0)
+        e1 = torch.exp(2j * np.pi * ((int(k1) * j1) % n1).to(torch.float64) / n1)
+        e2 = torch.exp(2j * np.pi * ((int(k2) * j2) % n2).to(torch.float64) / n2)
+        e12 = e1[:, None] * e2[None, :]
+        for i in range(n0):
+            out[i] += (e0[i] * e12).real.to(dtype)
+    return out

@@ -1,0 +1,132 @@
+"""Full-size workloads.
+
+* 1024^3, FP32 and FP64, in place: the turbulence-like field (random-phase
+  modes, |k|^(-11/6) for 1 <= |k| <= 512, seed 2) made by the FP64 oracle's
+  inverse and normalised to unit RMS; forward against the FP64 oracle
+  (FP32 <= 5e-6, FP64 <= 1e-13 relative L2) and the inverse round trip.
+* 2048^3 FP64 in place (68.8 GB) and 1536^3 FP32 (14.5 GB): too large for the
+  host oracle in a test, so checked by properties that hold at any size:
+  round trip, Parseval, and the closed-form spectrum of 8 seeded plane waves
+  (the transform of a sum of cosines is known exactly)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import TOL, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def turbulence_1024():
+    n = 1024
+    spec = synth.turbulence_spectrum(n, n, n, seed=2)
+    f = oracle.irfft3(spec, (n, n, n))
+    del spec
+    f /= np.sqrt(np.mean(f * f))
+    F = oracle.rfft3(f)
+    return f, F
+
+
+@pytest.mark.parametrize("name", ["f32", "f64"])
+def test_turbulence_1024_vs_oracle(turbulence_1024, name):
+    import torch
+    import paper_2202_12756_gb300 as fft3d
+    f, F_ref = turbulence_1024
+    n = 1024
+    dt = torch.float32 if name == "f32" else torch.float64
+    plan = fft3d.get_plan((n, n, n), dt, "cuda")
+    buf = plan.empty_padded()
+    buf[..., :n].copy_(torch.from_numpy(f))           # rounded once for FP32
+    fin = buf[..., :n].cpu().numpy().astype(np.float64)
+    X = plan.r2c_(buf)
+    torch.cuda.synchronize()
+    Xh = X.cpu().numpy().astype(np.complex128)
+    # the FP32 run is judged against the oracle of its own (rounded) input
+    ref = F_ref if name == "f64" else oracle.rfft3(fin)
+    err = rel_l2(Xh, ref)
+    print(f"1024^3 {name} r2c rel-L2 vs FP64 oracle: {err:.3e} (vs unrounded input: {rel_l2(Xh, F_ref):.3e})")
+    assert err <= TOL[name]
+    del Xh
+    plan.c2r_(buf)
+    torch.cuda.synchronize()
+    back = buf[..., :n].cpu().numpy().astype(np.float64)
+    err_rt = rel_l2(back, fin)
+    print(f"1024^3 {name} round trip rel-L2: {err_rt:.3e}")
+    assert err_rt <= TOL[name]
+
+
+def _plane_sum(fn, n0):
+    """sum over k0 planes of fn(i) (keeps temporaries at one plane)."""
+    return sum(fn(i) for i in range(n0))
+
+
+def _closed_form_checks(n, dt, seed, tol_rt, tol_pw):
+    """Round trip, Parseval and plane waves at n^3, with every reduction done
+    one plane at a time (no full-size temporaries besides one copy)."""
+    import torch
+    import paper_2202_12756_gb300 as fft3d
+    torch.cuda.empty_cache()
+    shape = (n, n, n)
+    plan = fft3d.get_plan(shape, dt, "cuda")
+    buf = plan.empty_padded()
+    view = buf[..., :n]
+    synth.uniform_field_device(shape, seed, "cuda", dtype=dt, out=view)
+    ref = view.clone()
+    lhs = _plane_sum(lambda i: (ref[i].double() ** 2).sum().item(), n)
+    X = plan.r2c_(buf)
+
+    def parseval_plane(i):
+        p = X[i].real.double() ** 2 + X[i].imag.double() ** 2
+        return (2.0 * p.sum() - p[:, 0].sum() - p[:, n // 2].sum()).item()
+
+    rhs = _plane_sum(parseval_plane, n) / float(n) ** 3
+    assert abs(lhs - rhs) <= tol_rt * lhs, (lhs, rhs)
+    plan.c2r_(buf)
+    num = _plane_sum(lambda i: ((view[i].double() - ref[i].double()) ** 2).sum().item(), n)
+    rt = (num / lhs) ** 0.5
+    assert rt <= tol_rt, rt
+    del ref
+    torch.cuda.empty_cache()
+    # plane waves: the spectrum of a sum of cosines is exactly N^3/2 at +-k
+    kv = synth.plane_wave_vectors(seed, count=8, kmax=n // 2)
+    view.zero_()
+    synth.plane_waves_device(shape, kv, "cuda", dtype=dt, out=view)
+    X = plan.r2c_(buf)
+    expect = {}
+    for k in kv:
+        for s in (1, -1):
+            q = ((s * k[0]) % n, (s * k[1]) % n, (s * k[2]) % n)
+            if q[2] <= n // 2:
+                expect[q] = expect.get(q, 0.0) + float(n) ** 3 / 2
+    for q, v in expect.items():
+        X[q] -= v
+    dev = max(X[i].abs().max().item() for i in range(n))
+    torch.cuda.synchronize()
+    assert dev <= tol_pw * float(n) ** 3, dev / float(n) ** 3
+    del X, view, buf
+    torch.cuda.empty_cache()
+    return rt
+
+
+def test_2048_cubed_fp64_closed_forms():
+    import torch
+    rt = _closed_form_checks(2048, torch.float64, 4, 1e-13, 1e-12)
+    print(f"2048^3 f64 round trip rel-L2 {rt:.3e}")
+
+
+def test_1536_cubed_fp32_closed_forms():
+    import torch
+    rt = _closed_form_checks(1536, torch.float32, 5, 5e-6, 1e-5)
+    print(f"1536^3 f32 round trip rel-L2 {rt:.3e}")
+
+
+@pytest.mark.parametrize("shape", [(96, 1536, 1536), (1536, 96, 96)], ids=lambda s: "x".join(map(str, s)))
+def test_1536_lengths_vs_oracle(shape):
+    """Oracle parity at the 1536-point lengths of the 1536^3 workload."""
+    import torch
+    import paper_2202_12756_gb300 as fft3d
+    from gpu_util import gpu_r2c, np_round
+    f = np_round(synth.uniform_field(shape, 6), "f32")
+    assert rel_l2(gpu_r2c(f, "f32"), oracle.rfft3(f)) <= TOL["f32"]

@@ -135,3 +135,35 @@ def test_plane_waves_512_fp64():
     assert np.max(np.abs((F - F_noise) - W)) < 1e-9 * np.prod(shape)
     back = gpu_c2r(F, shape, "f64")
     assert rel_l2(back, f) <= TOL["f64"]
+
+
+FUSED_SHAPES = [(4, 512, 512), (2, 1024, 1024), (3, 768, 768), (2, 1536, 1536), (1, 2048, 2048),
+                (6, 1024, 1024)]
+
+
+@pytest.mark.parametrize("shape", FUSED_SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_fused_plane_pass_parity(shape):
+    """Float plans with (N1, N2) in the fused set can run axes 2 and 1 as one
+    persistent kernel (planes handed over through L2); same results bar."""
+    import torch
+    import paper_2202_12756_gb300 as fft3d
+    plan = fft3d.get_plan(shape, torch.float32, "cuda")
+    plan.set_fused(True)
+    try:
+        assert plan.info()["fused_plane_pass"]
+        for inplace in (False, True):
+            check_pair(shape, "f32", inplace, seed=7)
+        assert plan.status() == 0
+    finally:
+        plan.set_fused(False)
+
+
+def test_fused_plane_pass_not_offered_elsewhere():
+    import torch
+    import paper_2202_12756_gb300 as fft3d
+    for shape, dt in (((8, 256, 256), torch.float32), ((4, 512, 512), torch.float64), ((4, 512, 256), torch.float32)):
+        plan = fft3d.Plan(shape, dt)
+        with pytest.raises(fft3d.FFT3DError) as e:
+            plan.set_fused(True)
+        assert e.value.status == fft3d.FFT3D_ERR_SIZE
+        assert not plan.info()["fused_plane_pass"]
