@@ -86,7 +86,9 @@ int fft3d_plan_destroy(fft3d_plan plan);
  * Forward R2C, Eq. 1 (unnormalised, sign -).
  *   in_real:  real array (dense [N0][N1][N2], or padded when in_real == out_cplx)
  *   out_cplx: complex array [N0][N1][N2/2+1]
- * Out-of-place calls never write in_real.
+ * Out-of-place calls never write in_real and read it exactly once, in the
+ * first (contiguous) pass, so it may be device-accessible host memory (see
+ * fft3d_exec_c2r_overwrite).
  */
 int fft3d_exec_r2c(fft3d_plan plan, const void *in_real, void *out_cplx, void *stream);
 
@@ -101,6 +103,20 @@ int fft3d_exec_r2c(fft3d_plan plan, const void *in_real, void *out_cplx, void *s
  * k2 = N2/2 column, which does not fit in the dense real output).
  */
 int fft3d_exec_c2r(fft3d_plan plan, const void *in_cplx, void *out_real, void *stream);
+
+/*
+ * The same inverse as fft3d_exec_c2r, out of place, using the input array as
+ * work space: the axis-0 and axis-1 passes run in place on inout_cplx (which
+ * is overwritten), and out_real (dense [N0][N1][N2]) is written exactly once,
+ * by the last, contiguous pass, and never read.  Needs no plan scratch.
+ * Because only that pass touches them, in_real of fft3d_exec_r2c and out_real
+ * here may be host memory the GPU can access directly (pinned / registered
+ * host memory, or any system memory on a coherent CPU-GPU node): the first
+ * and last passes then stream the field over the CPU-GPU link while the
+ * strided passes stay in HBM.  With inout_cplx == out_real this is the
+ * in-place inverse.
+ */
+int fft3d_exec_c2r_overwrite(fft3d_plan plan, void *inout_cplx, void *out_real, void *stream);
 
 /*
  * Adjoint (vector-Jacobian product) of fft3d_exec_r2c with respect to its

@@ -46,6 +46,7 @@ EXPORTED = (
     "fft3d_plan_last_error", "fft3d_supported_length", "fft3d_plan_set_profiling",
     "fft3d_plan_profile_read", "fft3d_plan_launch_count", "fft3d_exec_c2r_noalloc",
     "fft3d_plan_status", "fft3d_plan_set_debug", "fft3d_plan_info", "fft3d_plan_set_fused",
+    "fft3d_exec_c2r_overwrite",
 )
 
 
@@ -72,7 +73,8 @@ def _declare(lib):
     I64 = ctypes.c_int64
     lib.fft3d_plan_create.argtypes = [ctypes.POINTER(P), I64, I64, I64, ctypes.c_int]
     lib.fft3d_plan_destroy.argtypes = [P]
-    for f in ("fft3d_exec_r2c", "fft3d_exec_c2r", "fft3d_exec_r2c_adjoint", "fft3d_exec_c2r_adjoint"):
+    for f in ("fft3d_exec_r2c", "fft3d_exec_c2r", "fft3d_exec_r2c_adjoint", "fft3d_exec_c2r_adjoint",
+              "fft3d_exec_c2r_overwrite"):
         getattr(lib, f).argtypes = [P, P, P, P]
     lib.fft3d_strerror.argtypes = [ctypes.c_int]
     lib.fft3d_strerror.restype = ctypes.c_char_p
@@ -145,6 +147,11 @@ def fft3d_exec_r2c(plan, in_real, out_cplx, stream):
 
 def fft3d_exec_c2r(plan, in_cplx, out_real, stream):
     _check(load_library().fft3d_exec_c2r(plan, in_cplx, out_real, stream), "fft3d_exec_c2r", plan)
+
+
+def fft3d_exec_c2r_overwrite(plan, inout_cplx, out_real, stream):
+    _check(load_library().fft3d_exec_c2r_overwrite(plan, inout_cplx, out_real, stream),
+           "fft3d_exec_c2r_overwrite", plan)
 
 
 def fft3d_exec_r2c_adjoint(plan, in_cplx, out_real, stream):
@@ -289,10 +296,11 @@ class Plan:
         n0, n1, n2 = self.shape
         return _torch().empty((n0, n1, 2 * (n2 // 2 + 1)), dtype=self.real_dtype, device=self.device)
 
-    def _check_real(self, t, padded=False):
+    def _check_real(self, t, padded=False, host_ok=False):
         n0, n1, n2 = self.shape
         want = (n0, n1, 2 * (n2 // 2 + 1)) if padded else self.shape
-        if t.dtype != self.real_dtype or tuple(t.shape) != want or not t.is_contiguous() or t.device != self.device:
+        where_ok = t.device == self.device or (host_ok and t.device.type == "cpu" and t.is_pinned())
+        if t.dtype != self.real_dtype or tuple(t.shape) != want or not t.is_contiguous() or not where_ok:
             raise FFT3DError(FFT3D_ERR_ARG, "real tensor", f"need contiguous {want} {self.real_dtype} on {self.device}")
 
     def _check_cplx(self, t):
@@ -301,9 +309,9 @@ class Plan:
             raise FFT3DError(FFT3D_ERR_ARG, "complex tensor",
                              f"need contiguous {self.half_shape} {self.complex_dtype} on {self.device}")
 
-    # out-of-place
+    # out-of-place; x may also be a pinned host tensor (read once, by the first pass)
     def r2c(self, x, out=None):
-        self._check_real(x)
+        self._check_real(x, host_ok=True)
         out = self.empty_complex() if out is None else out
         self._check_cplx(out)
         self._run(fft3d_exec_r2c, x, out)
@@ -314,6 +322,15 @@ class Plan:
         out = self.empty_real() if out is None else out
         self._check_real(out)
         self._run(fft3d_exec_c2r, X, out)
+        return out
+
+    def c2r_overwrite(self, X, out=None):
+        """Inverse that uses X as work space (X is overwritten); `out` may be a
+        pinned host tensor (written once, by the last pass)."""
+        self._check_cplx(X)
+        out = self.empty_real() if out is None else out
+        self._check_real(out, host_ok=True)
+        self._run(fft3d_exec_c2r_overwrite, X, out)
         return out
 
     def r2c_adjoint(self, G, out=None):

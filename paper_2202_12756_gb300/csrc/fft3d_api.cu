@@ -282,13 +282,18 @@ int forward_pipeline(fft3d_plan p, const void *in, void *out, cudaStream_t st, d
 // C2R pipeline: x -> y -> z (C2R with edge weight `we` and output scale `s`).
 // Out of place, the x-pass writes the split layout (k2 < M rows in the
 // output buffer, k2 = M in the plan's scratch plane) so the input survives.
-int inverse_pipeline(fft3d_plan p, const void *in, void *out, cudaStream_t st, double we, double s)
+int inverse_pipeline(fft3d_plan p, const void *in, void *out, cudaStream_t st, double we, double s,
+                     bool overwrite_input = false)
 {
     const bool inplace = (in == out);
     const CLayout src = {const_cast<void *>(in), nullptr, 0};
-    const CLayout dst = inplace ? src : CLayout{out, p->nyq, 1};
+    // Out of place, the axis-0 and axis-1 passes work either in the output
+    // (split layout, input preserved) or, when the caller allows it, in the
+    // input itself (standard layout; the output is then written only once,
+    // by the last pass).
+    const CLayout dst = (inplace || overwrite_input) ? src : CLayout{out, p->nyq, 1};
     int rc;
-    if (p->n0 > 1 || !inplace) {
+    if (p->n0 > 1 || dst.main != src.main) {
         int64_t tiles;
         const ColArgs a = xpass_args(p, src, dst, 1, &tiles);
         rc = run_pass(p, K_C2R_X, st, [&] { return col_launch(p, (int)p->n0, a, tiles, p->tw0, st); });
@@ -469,6 +474,14 @@ int fft3d_exec_c2r(fft3d_plan p, const void *in_cplx, void *out_real, void *stre
     if (rc) return rc;
     const double s = 1.0 / ((double)p->n0 * (double)p->n1 * (double)p->n2);
     return inverse_pipeline(p, in_cplx, out_real, (cudaStream_t)stream, 1.0, s);
+}
+
+int fft3d_exec_c2r_overwrite(fft3d_plan p, void *inout_cplx, void *out_real, void *stream)
+{
+    int rc = check_exec(p, inout_cplx, out_real, false);
+    if (rc) return rc;
+    const double s = 1.0 / ((double)p->n0 * (double)p->n1 * (double)p->n2);
+    return inverse_pipeline(p, inout_cplx, out_real, (cudaStream_t)stream, 1.0, s, true);
 }
 
 int fft3d_exec_r2c_adjoint(fft3d_plan p, const void *in_cplx, void *out_real, void *stream)

@@ -167,3 +167,45 @@ def test_fused_plane_pass_not_offered_elsewhere():
             plan.set_fused(True)
         assert e.value.status == fft3d.FFT3D_ERR_SIZE
         assert not plan.info()["fused_plane_pass"]
+
+
+@pytest.mark.parametrize("shape", [(16, 24, 32), (64, 32, 48), (1, 4, 8), (8, 1024, 12)],
+                         ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("name", ["f64", "f32"])
+def test_c2r_overwrite(shape, name):
+    """Inverse that uses its input as work space: same result as the
+    input-preserving inverse; the dense output is written by the last pass."""
+    import torch
+    import paper_2202_12756_gb300 as fft3d
+    from gpu_util import torch_dtype
+    dt = torch_dtype(name)
+    plan = fft3d.get_plan(shape, dt, "cuda")
+    G = synth.random_half_spectrum(shape, 71)
+    if name == "f32":
+        G = G.astype(np.complex64).astype(np.complex128)
+    X = torch.from_numpy(G).to(fft3d.complex_of(dt)).cuda()
+    out = torch.full(shape, float("nan"), dtype=dt, device="cuda")
+    plan.c2r_overwrite(X, out)
+    torch.cuda.synchronize()
+    assert rel_l2(out.cpu().numpy(), oracle.irfft3(G, shape)) <= TOL[name]
+
+
+@pytest.mark.parametrize("name", ["f64", "f32"])
+def test_host_resident_field(name):
+    """Forward from, and overwrite-inverse into, pinned host memory (read and
+    written directly by the first and last passes)."""
+    import torch
+    import paper_2202_12756_gb300 as fft3d
+    from gpu_util import torch_dtype
+    dt = torch_dtype(name)
+    shape = (32, 64, 128)
+    plan = fft3d.get_plan(shape, dt, "cuda")
+    f = np_round(synth.uniform_field(shape, 72), name)
+    host_in = torch.from_numpy(f).to(dt).pin_memory()
+    host_out = torch.full(shape, float("nan"), dtype=dt).pin_memory()
+    X = plan.r2c(host_in)
+    torch.cuda.synchronize()
+    assert rel_l2(X.cpu().numpy(), oracle.rfft3(f)) <= TOL[name]
+    plan.c2r_overwrite(X, host_out)
+    torch.cuda.synchronize()
+    assert rel_l2(host_out.numpy(), f) <= TOL[name]
