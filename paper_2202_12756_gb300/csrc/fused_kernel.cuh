@@ -149,8 +149,8 @@ fused_plane_kernel(FusedArgs a, const typename cvec<R>::T *__restrict__ tw_y,
             else zc2r_lines<R, M, line_E(M), LPB, true>(a.z, line0, smem_raw, tw_z, rot);
         } else {
             const int64_t tile = plane * a.yi + idx;
-            if (a.forward) col_tile<R, N1, line_E(N1), W, true>(a.y, tile, smem_raw, tw_y);
-            else col_tile<R, N1, line_E(N1), W, false>(a.y, tile, smem_raw, tw_y);
+            if (a.forward) col_tile<R, N1, line_E(N1), W, true, false>(a.y, tile, smem_raw, tw_y);
+            else col_tile<R, N1, line_E(N1), W, false, true>(a.y, tile, smem_raw, tw_y);
         }
 
         if (prod) {

@@ -87,12 +87,20 @@ template <typename R, int L> inline cudaError_t col_prepare_t()
 {
     PassGeom g;
     col_geom_t<R, L>(&g);
-    if constexpr (col_pipe<R, L>())
-        return cudaFuncSetAttribute(colpass_pipe_kernel<R, L, col_E<R, L>(), col_W<R, L>()>,
+    cudaError_t e;
+    if constexpr (col_pipe<R, L>()) {
+        e = cudaFuncSetAttribute(colpass_pipe_kernel<R, L, col_E<R, L>(), col_W<R, L>(), false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(colpass_pipe_kernel<R, L, col_E<R, L>(), col_W<R, L>(), true>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
-    else
-        return cudaFuncSetAttribute(colpass_kernel<R, L, col_E<R, L>(), col_W<R, L>()>,
+    } else {
+        e = cudaFuncSetAttribute(colpass_kernel<R, L, col_E<R, L>(), col_W<R, L>(), false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(colpass_kernel<R, L, col_E<R, L>(), col_W<R, L>(), true>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+    }
 }
 
 template <typename R, int M> inline cudaError_t z_prepare_t()
@@ -131,11 +139,14 @@ inline cudaError_t col_launch_t(const ColArgs &a, int64_t tiles, const void *tw,
     col_geom_t<R, L>(&g);
     typedef const typename cvec<R>::T *TW;
     if constexpr (col_pipe<R, L>()) {
-        auto k = colpass_pipe_kernel<R, L, col_E<R, L>(), col_W<R, L>()>;
+        auto k = a.inverse ? colpass_pipe_kernel<R, L, col_E<R, L>(), col_W<R, L>(), true>
+                           : colpass_pipe_kernel<R, L, col_E<R, L>(), col_W<R, L>(), false>;
         const int grid = persistent_grid(k, g.threads, g.smem, tiles);
         k<<<grid, g.threads, g.smem, st>>>(a, (TW)tw, tiles);
     } else {
-        colpass_kernel<R, L, col_E<R, L>(), col_W<R, L>()><<<(unsigned)tiles, g.threads, g.smem, st>>>(a, (TW)tw);
+        auto k = a.inverse ? colpass_kernel<R, L, col_E<R, L>(), col_W<R, L>(), true>
+                           : colpass_kernel<R, L, col_E<R, L>(), col_W<R, L>(), false>;
+        k<<<(unsigned)tiles, g.threads, g.smem, st>>>(a, (TW)tw);
     }
     return cudaGetLastError();
 }

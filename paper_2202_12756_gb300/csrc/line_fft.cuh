@@ -249,57 +249,79 @@ __device__ __forceinline__ void line_stage_compute(typename cvec<R>::T *v, int j
     }
 }
 
-// destination index of slot q + m Q after stage S
-template <int L, int E, int S> __device__ __forceinline__ int line_stage_dest(int j, int q, int m)
-{
-    constexpr int NT = L / E;
-    constexpr int RS = line_radix(L, E, S);
-    constexpr int NS = line_ns(L, E, S);
-    const int b = j + q * NT;
-    return (b / NS) * NS * RS + (b % NS) + m * NS;
-}
-
 struct NoHook {
     __device__ __forceinline__ void operator()() const {}
 };
 
-// Exchange after stage S: every slot's value goes to the thread that owns
-// its destination index.  `hook` runs once, right after the first barrier
-// (when every thread's earlier shared-memory reads have completed).
+// Exchange objects address a line's (or column's) buffer by row.  A padded
+// buffer (kPadShift = P >= 0) stores row r at r + (r >> P); the padding keeps
+// strided writes free of bank conflicts.  A row is passed as base + off with
+// `off` known at compile time; when (base mod 2^P) + (off mod 2^P) < 2^P for
+// every use (LIN), pad(base + off) = pad(base) + off + (off >> P), so the
+// per-element address is a constant offset from a per-thread base.
+template <int P> __host__ __device__ constexpr bool pad_linear(int ns, int rs)
+{
+    return P < 0 || ns % (1 << P) == 0 || (ns == 1 && rs % (1 << P) == 0);
+}
+template <int P> __host__ __device__ constexpr bool pad_linear_reads(int nt)
+{
+    return P < 0 || nt % (1 << P) == 0 || (1 << P) % nt == 0;
+}
+template <int P, bool LIN> __device__ __forceinline__ int pad_row(int base, int off)
+{
+    if constexpr (P < 0) return base + off;
+    else if constexpr (LIN) return base + (base >> P) + off + (off >> P);
+    else return base + off + ((base + off) >> P);
+}
+
+// Exchange after stage S: slot q + m Q (butterfly b = j + q NT, output m)
+// goes to row (b / Ns) Ns R + (b mod Ns) + m Ns; thread j then reads rows
+// j + i NT.  `hook` runs once, right after the first barrier (when every
+// thread's earlier shared-memory reads have completed).
 template <typename R, int L, int E, int S, class Ex, class Hook>
 __device__ __forceinline__ void line_exchange(typename cvec<R>::T *v, int j, Ex &ex, const Hook &hook)
 {
     constexpr int NT = L / E;
     constexpr int RS = line_radix(L, E, S);
+    constexpr int NS = line_ns(L, E, S);
     constexpr int Q = E / RS;
+    constexpr int P = Ex::kPadShift;
+    constexpr bool LW = pad_linear<P>(NS, RS);
+    constexpr bool LR = pad_linear_reads<P>(NT);
+    int base[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int b = j + q * NT;
+        base[q] = (b / NS) * NS * RS + (b % NS);
+    }
     if constexpr (Ex::kSplit) {
         // real parts, then imaginary parts, through a buffer of half the size
 #pragma unroll
         for (int q = 0; q < Q; ++q)
 #pragma unroll
-            for (int m = 0; m < RS; ++m) ex.put_real(line_stage_dest<L, E, S>(j, q, m), v[q + m * Q].x);
+            for (int m = 0; m < RS; ++m) ex.put_real(pad_row<P, LW>(base[q], m * NS), v[q + m * Q].x);
         ex.sync();
         hook();
 #pragma unroll
-        for (int i = 0; i < E; ++i) v[i].x = ex.get_real(j + i * NT);
+        for (int i = 0; i < E; ++i) v[i].x = ex.get_real(pad_row<P, LR>(j, i * NT));
         ex.sync();
 #pragma unroll
         for (int q = 0; q < Q; ++q)
 #pragma unroll
-            for (int m = 0; m < RS; ++m) ex.put_real(line_stage_dest<L, E, S>(j, q, m), v[q + m * Q].y);
+            for (int m = 0; m < RS; ++m) ex.put_real(pad_row<P, LW>(base[q], m * NS), v[q + m * Q].y);
         ex.sync();
 #pragma unroll
-        for (int i = 0; i < E; ++i) v[i].y = ex.get_real(j + i * NT);
+        for (int i = 0; i < E; ++i) v[i].y = ex.get_real(pad_row<P, LR>(j, i * NT));
         ex.sync();
     } else {
 #pragma unroll
         for (int q = 0; q < Q; ++q)
 #pragma unroll
-            for (int m = 0; m < RS; ++m) ex.put(line_stage_dest<L, E, S>(j, q, m), v[q + m * Q]);
+            for (int m = 0; m < RS; ++m) ex.put(pad_row<P, LW>(base[q], m * NS), v[q + m * Q]);
         ex.sync();
         hook();
 #pragma unroll
-        for (int i = 0; i < E; ++i) v[i] = ex.get(j + i * NT);
+        for (int i = 0; i < E; ++i) v[i] = ex.get(pad_row<P, LR>(j, i * NT));
         ex.sync();
     }
 }

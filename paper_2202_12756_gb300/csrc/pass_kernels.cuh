@@ -70,6 +70,7 @@ __device__ __forceinline__ void layout_column(const CLayout &l, int64_t n1, int6
 // conflict-free without padding.
 template <typename C, int W> struct ColEx {
     static constexpr bool kSplit = false;
+    static constexpr int kPadShift = -1;
     C *sm;
     int c;
     __device__ __forceinline__ void put(int row, C v) { sm[row * W + c] = v; }
@@ -78,7 +79,9 @@ template <typename C, int W> struct ColEx {
 };
 
 // Which column lane c of tile t owns, and where it lives in the source and
-// destination layouts.  Returns false for lanes past the last column.
+// destination layouts.  Lanes past the last column get the last column's
+// address (so every load is in bounds) and `false`: they compute on a copy
+// and store nothing.  Columns never mix, so this is harmless.
 template <typename C, int W>
 __device__ __forceinline__ bool col_decode(const ColArgs &a, int64_t t, int c, C *&sp, int64_t &ss, C *&dp,
                                            int64_t &ds)
@@ -86,27 +89,30 @@ __device__ __forceinline__ bool col_decode(const ColArgs &a, int64_t t, int c, C
     int64_t k0 = 0, k1 = 0, k2 = 0;
     bool valid;
     if (a.axis == 0) {
-        const int64_t f = t * W + c;  // flat (k1, k2) index
-        valid = f < a.n1 * (a.m + 1);
+        const int64_t total = a.n1 * (a.m + 1);
+        int64_t f = t * W + c;  // flat (k1, k2) index
+        valid = f < total;
+        f = valid ? f : total - 1;
         k1 = f / (a.m + 1);
         k2 = f - k1 * (a.m + 1);
     } else if (a.nyq_in_plane) {
         k0 = t / a.tiles_per_plane;
         k2 = (t - k0 * a.tiles_per_plane) * W + c;
         valid = k2 <= a.m;
+        k2 = valid ? k2 : a.m;
     } else if (t < a.tiles_main) {
         k0 = t / a.tiles_per_plane;
         k2 = (t - k0 * a.tiles_per_plane) * W + c;
         valid = k2 < a.m;
+        k2 = valid ? k2 : a.m - 1;
     } else {  // k2 = M column of W consecutive planes
         k0 = (t - a.tiles_main) * W + c;
         k2 = a.m;
         valid = k0 < a.n0;
+        k0 = valid ? k0 : a.n0 - 1;
     }
-    if (valid) {
-        layout_column<C>(a.src, a.n1, a.m, a.axis, k0, k1, k2, sp, ss);
-        layout_column<C>(a.dst, a.n1, a.m, a.axis, k0, k1, k2, dp, ds);
-    }
+    layout_column<C>(a.src, a.n1, a.m, a.axis, k0, k1, k2, sp, ss);
+    layout_column<C>(a.dst, a.n1, a.m, a.axis, k0, k1, k2, dp, ds);
     return valid;
 }
 
@@ -116,11 +122,11 @@ __device__ __forceinline__ bool col_decode(const ColArgs &a, int64_t t, int c, C
 // bank conflicts (W reals = 64 bytes per row).
 template <typename R, int W> struct ColSplitEx {
     static constexpr bool kSplit = true;
+    static constexpr int kPadShift = 5;  // rows arrive padded: r + (r >> 5)
     R *sm;
     int c;
-    __device__ __forceinline__ int idx(int row) const { return (row + (row >> 5)) * W + c; }
-    __device__ __forceinline__ void put_real(int row, R v) { sm[idx(row)] = v; }
-    __device__ __forceinline__ R get_real(int row) const { return sm[idx(row)]; }
+    __device__ __forceinline__ void put_real(int prow, R v) { sm[prow * W + c] = v; }
+    __device__ __forceinline__ R get_real(int prow) const { return sm[prow * W + c]; }
     __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 
@@ -130,7 +136,7 @@ template <typename C> __device__ __forceinline__ C load_cg(const C *p) { return 
 
 // One column tile (W columns x L rows) with the block's threads; the tile is
 // loaded straight into registers.  CG selects L2-only loads.
-template <typename R, int L, int E, int W, bool CG>
+template <typename R, int L, int E, int W, bool CG, bool INV>
 __device__ __forceinline__ void col_tile(const ColArgs &a, int64_t tile, unsigned char *smem,
                                          const typename cvec<R>::T *__restrict__ tw)
 {
@@ -142,32 +148,35 @@ __device__ __forceinline__ void col_tile(const ColArgs &a, int64_t tile, unsigne
     int64_t ss = 0, ds = 0;
     const bool valid = col_decode<C, W>(a, tile, c, sp, ss, dp, ds);
 
+    const C *sj = sp + (int64_t)j * ss;
+    const int64_t sstep = (int64_t)NT * ss;
     C v[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) {
-        if (valid) v[i] = CG ? load_cg(sp + (int64_t)(j + i * NT) * ss) : sp[(int64_t)(j + i * NT) * ss];
-        else v[i] = cmake<C>(R(0), R(0));
-        if (a.inverse) v[i].y = -v[i].y;
+        v[i] = CG ? load_cg(sj + i * sstep) : sj[i * sstep];
+        if (INV) v[i].y = -v[i].y;
     }
     ColEx<C, W> ex{(C *)smem, c};
     line_fft<R, L, E>(v, j, tw, ex);
     if (valid) {
+        C *dj = dp + (int64_t)j * ds;
+        const int64_t dstep = (int64_t)NT * ds;
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             C o = v[i];
-            if (a.inverse) o.y = -o.y;
-            dp[(int64_t)(j + i * NT) * ds] = o;
+            if (INV) o.y = -o.y;
+            dj[i * dstep] = o;
         }
     }
 }
 
 // One tile per block.
-template <typename R, int L, int E, int W>
+template <typename R, int L, int E, int W, bool INV>
 __global__ void __launch_bounds__(W *(L / E))
 colpass_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    col_tile<R, L, E, W, false>(a, blockIdx.x, smem_raw, tw);
+    col_tile<R, L, E, W, false, INV>(a, blockIdx.x, smem_raw, tw);
 }
 
 template <int L> __host__ __device__ constexpr int split_rows() { return L + (L >> 5) + 1; }
@@ -194,7 +203,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // its slots after the first exchange barrier, when its reads of them have
 // completed.  The stage exchange uses a separate split (real / imaginary)
 // buffer.  Shared memory: L W complex (staging) + (L + L/32 + 1) W reals.
-template <typename R, int L, int E, int W>
+template <typename R, int L, int E, int W, bool INV>
 __global__ void __launch_bounds__(W *(L / E), (W * (L / E) >= 512 ? 1 : 512 / (W * (L / E))))
 colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64_t ntiles)
 {
@@ -208,12 +217,13 @@ colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
     ex.c = c;
 
     auto prefetch = [&](const C *sp, int64_t ss) {
+        const C *sj = sp + (int64_t)j * ss;
+        const int64_t sstep = (int64_t)NT * ss;
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             C *dst = stage + (j + i * NT) * W + c;
-            const C *src = sp + (int64_t)(j + i * NT) * ss;
-            if (sizeof(C) == 8) cp_async_8(dst, src);
-            else cp_async_16(dst, src);
+            if (sizeof(C) == 8) cp_async_8(dst, sj + i * sstep);
+            else cp_async_16(dst, sj + i * sstep);
         }
     };
 
@@ -221,7 +231,7 @@ colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
     C *sp = nullptr, *dp = nullptr;
     int64_t ss = 0, ds = 0;
     bool valid = t < ntiles && col_decode<C, W>(a, t, c, sp, ss, dp, ds);
-    if (valid) prefetch(sp, ss);
+    if (t < ntiles) prefetch(sp, ss);
     cp_async_commit();
     while (t < ntiles) {
         const int64_t tn = t + gridDim.x;
@@ -233,22 +243,24 @@ colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
         C v[E];
 #pragma unroll
         for (int i = 0; i < E; ++i) {
-            v[i] = valid ? stage[(j + i * NT) * W + c] : cmake<C>(R(0), R(0));
-            if (a.inverse) v[i].y = -v[i].y;
+            v[i] = stage[(j + i * NT) * W + c];
+            if (INV) v[i].y = -v[i].y;
         }
         // Stage the next tile into the same slots once these reads are
         // complete, i.e. after the first exchange barrier.
         auto next = [&]() {
-            if (validn) prefetch(spn, ssn);
+            if (tn < ntiles) prefetch(spn, ssn);
             cp_async_commit();
         };
         line_fft<R, L, E>(v, j, tw, ex, next);
         if (valid) {
+            C *dj = dp + (int64_t)j * ds;
+            const int64_t dstep = (int64_t)NT * ds;
 #pragma unroll
             for (int i = 0; i < E; ++i) {
                 C o = v[i];
-                if (a.inverse) o.y = -o.y;
-                dp[(int64_t)(j + i * NT) * ds] = o;
+                if (INV) o.y = -o.y;
+                dj[i * dstep] = o;
             }
         }
         t = tn;
@@ -274,12 +286,13 @@ struct ZArgs {
 
 // Per-line shared-memory exchange with one padding slot every 16 elements,
 // which makes the stride-16 writes of a radix-16 first stage conflict-free.
+// Indices arrive padded (i + (i >> 4), see pad_row).
 template <typename C, int NT> struct LineEx {
     static constexpr bool kSplit = false;
+    static constexpr int kPadShift = 4;
     C *sm;
-    __device__ __forceinline__ static int pad(int i) { return i + (i >> 4); }
-    __device__ __forceinline__ void put(int i, C v) { sm[pad(i)] = v; }
-    __device__ __forceinline__ C get(int i) const { return sm[pad(i)]; }
+    __device__ __forceinline__ void put(int pi, C v) { sm[pi] = v; }
+    __device__ __forceinline__ C get(int pi) const { return sm[pi]; }
     __device__ __forceinline__ void sync() const
     {
         if (NT <= 32) __syncwarp();
@@ -312,16 +325,19 @@ __device__ __forceinline__ void zr2c_lines(const ZArgs &a, int64_t line0, unsign
     line_fft<R, M, E>(v, j, tw, ex);
 
     // Hermitian post-process: needs Z[k] and Z[M - k] together
+    constexpr bool LR = pad_linear_reads<4>(NT);
+    constexpr bool LREV = NT % 16 == 0;  // M - j - i NT stays linear in i
 #pragma unroll
-    for (int i = 0; i < E; ++i) ex.put(j + i * NT, v[i]);
+    for (int i = 0; i < E; ++i) ex.put(pad_row<4, LR>(j, i * NT), v[i]);
     ex.sync();
     C *out = (C *)a.cplx.main + (active ? line : 0) * (M + 1);
     const R se = R(a.scale_edge), sm = R(a.scale_mid);
 #pragma unroll
     for (int i = 0; i < E; ++i) {
         const int k = j + i * NT;
-        const C z = ex.get(k);
-        const C zc = cconj(ex.get(k == 0 ? 0 : M - k));
+        const C z = ex.get(pad_row<4, LR>(j, i * NT));
+        const C zm = ex.get(pad_row<4, LREV>(M - j, -i * NT));  // Z[M - k]; k = 0 reads index M
+        const C zc = cconj((i == 0 && j == 0) ? z : zm);          // Z[(M - k) mod M]
         const C s = cadd(z, zc);                         // 2 E[k]
         const C d = cmul(__ldg(rot + k), csub(z, zc));   // 2i W^k O[k]
         // X[k] = (s - i d) / 2
@@ -359,21 +375,23 @@ __device__ __forceinline__ void zc2r_lines(const ZArgs &a, int64_t line0, unsign
         src = (const C *)a.cplx.main + l * (M + 1);
         nyq = src + M;
     }
+    constexpr bool LR = pad_linear_reads<4>(NT);
+    constexpr bool LREV = NT % 16 == 0;
     C v[E];
 #pragma unroll
     for (int i = 0; i < E; ++i)
         v[i] = active ? (CG ? load_cg(src + j + i * NT) : src[j + i * NT]) : cmake<C>(R(0), R(0));
 #pragma unroll
-    for (int i = 0; i < E; ++i) ex.put(j + i * NT, v[i]);
-    if (j == 0) ex.put(M, active ? (CG ? load_cg(nyq) : *nyq) : cmake<C>(R(0), R(0)));
+    for (int i = 0; i < E; ++i) ex.put(pad_row<4, LR>(j, i * NT), v[i]);
+    if (j == 0) ex.put(pad_row<4, true>(M, 0), active ? (CG ? load_cg(nyq) : *nyq) : cmake<C>(R(0), R(0)));
     ex.sync();
 
     const R we = R(a.scale_edge);
 #pragma unroll
     for (int i = 0; i < E; ++i) {
         const int k = j + i * NT;
-        C x = ex.get(k);
-        C y = ex.get(M - k);  // k = 0 pairs with X[M]
+        C x = ex.get(pad_row<4, LR>(j, i * NT));
+        C y = ex.get(pad_row<4, LREV>(M - j, -i * NT));  // X[M - k]; k = 0 pairs with X[M]
         if (k == 0) {
             // only the real parts of the k2 = 0 and k2 = M entries enter
             x = cmake<C>(we * x.x, R(0));
