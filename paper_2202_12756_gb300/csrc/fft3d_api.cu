@@ -10,8 +10,11 @@
 // reverse order", Sec. 3) with the 1/N^3 normalisation fused into the last.
 #include <cuda_runtime.h>
 
+#include <cuda.h>  // CUtensorMap and its enums (types only; the encoder comes from the driver at run time)
+
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -57,6 +60,7 @@ struct fft3d_plan_s {
     PassGeom gf;          // fused geometry (per_block = W of its Y tiles)
     int fz_lines;         // lines per fused Z item
     unsigned *sync;       // device: fused-pass tickets, flags, per-plane counters
+    unsigned *status;     // device: sticky error flag of the plan's kernels
     long long spin_limit;
     int inject_stall;
     char err[512];
@@ -133,9 +137,61 @@ template <class F> int run_pass(fft3d_plan p, int kind, cudaStream_t st, F &&lau
 }
 
 cudaError_t col_launch(const fft3d_plan_s *p, int L, const ColArgs &a, int64_t tiles, const void *tw,
-                       cudaStream_t st)
+                       cudaStream_t st, const CUtensorMap *tmap = nullptr, const CUtensorMap *tmap2 = nullptr)
 {
-    return p->dtype == FFT3D_F32 ? col_launch_f32(L, a, tiles, tw, st) : col_launch_f64(L, a, tiles, tw, st);
+    return p->dtype == FFT3D_F32 ? col_launch_f32(L, a, tiles, tw, tmap, tmap2, st)
+                                 : col_launch_f64(L, a, tiles, tw, tmap, tmap2, st);
+}
+
+// cuTensorMapEncodeTiled, fetched from the driver once (no libcuda link).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &ptr, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)ptr;
+    });
+    return fn;
+}
+
+// 2D tensor map over 8-byte elements (one float complex): `inner` elements
+// per row, `rows` rows `pitch` elements apart, boxes of box_w x 256.
+bool tensor_map_2d(const void *base, int64_t inner, int64_t rows, int64_t pitch, int box_w, CUtensorMap *map)
+{
+    EncodeTiledFn fn = encode_tiled_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch * 8};
+    const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)kTmaBoxRows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// TMA mode of a pipelined column pass over `src` (see colpass_pipe_kernel):
+// 0 = per-element copies; 1 = one map over 16-byte aligned rows; 2 = even /
+// odd row maps (y-pass rows of odd complex pitch).  Needs float, the
+// pipelined kernel for this length, a standard layout at a 16-byte aligned
+// base, full tiles, and L a multiple of 512.
+int bulk_mode(const fft3d_plan_s *p, const CLayout &src, int axis, int64_t w)
+{
+    const PassGeom &g = axis == 0 ? p->g0 : p->g1;
+    const int64_t L = axis == 0 ? p->n0 : p->n1;
+    if (!g.persistent || p->dtype != FFT3D_F32 || src.split || ((uintptr_t)src.main & 15) ||
+        L % (2 * kTmaBoxRows) != 0)
+        return 0;
+    if (axis == 0) return ((p->n1 * p->m1) % 2 == 0 && (p->n1 * p->m1) % w == 0) ? 1 : 0;
+    if (p->m % w != 0) return 0;
+    return (p->m1 % 2 == 0) ? 1 : 2;
 }
 
 // y-pass (axis 1) tiles: per k0 plane, ceil(M / W) tiles of the k2 < M
@@ -154,6 +210,8 @@ ColArgs ypass_args(const fft3d_plan_s *p, CLayout src, CLayout dst, int inverse,
     a.tiles_per_plane = (p->m + w - 1) / w;
     a.tiles_main = p->n0 * a.tiles_per_plane;
     a.nyq_in_plane = 0;
+    a.bulk = bulk_mode(p, src, 1, w);
+    a.err = p->status;
     *tiles = a.tiles_main + (p->n0 + w - 1) / w;
     return a;
 }
@@ -174,6 +232,8 @@ ColArgs xpass_args(const fft3d_plan_s *p, CLayout src, CLayout dst, int inverse,
     a.tiles_main = *tiles;
     a.tiles_per_plane = 0;
     a.nyq_in_plane = 0;
+    a.bulk = bulk_mode(p, src, 0, w);
+    a.err = p->status;
     return a;
 }
 
@@ -196,6 +256,8 @@ int run_fused(fft3d_plan p, int kind, const ZArgs &z, CLayout ylayout, int forwa
     f.y.tiles_per_plane = f.yi;
     f.y.tiles_main = p->n0 * f.yi;
     f.y.nyq_in_plane = 1;
+    f.y.bulk = 0;
+    f.y.err = p->status;
     f.n0 = p->n0;
     f.zi = p->n1 / p->fz_lines;
 #ifndef FFT3D_FUSED_LAG
@@ -211,6 +273,41 @@ int run_fused(fft3d_plan p, int kind, const ZArgs &z, CLayout ylayout, int forwa
     if (e != cudaSuccess) return set_err(p, FFT3D_ERR_CUDA, "cudaMemsetAsync", e);
     return run_pass(p, kind, st,
                     [&] { return fused_launch_f32((int)p->n1, (int)p->m, f, p->tw1f, p->twz, p->rot, st); });
+}
+
+// Column-pass launch; full float tiles go through TMA when the layout allows it.
+int run_colpass(fft3d_plan p, int kind, ColArgs a, int64_t tiles, int L, const void *tw, cudaStream_t st)
+{
+    CUtensorMap map, map2;
+    const CUtensorMap *mp = nullptr, *mp2 = nullptr;
+    const int w = (int)(a.axis == 0 ? p->g0.per_block : p->g1.per_block);
+    bool ok = true;
+    if (a.bulk == 1 && a.axis == 0) {
+        ok = tensor_map_2d(a.src.main, p->n1 * p->m1, p->n0, p->n1 * p->m1, w, &map);
+    } else if (a.bulk == 1) {
+        ok = tensor_map_2d(a.src.main, p->m1, p->n0 * p->n1, p->m1, w, &map);
+    } else if (a.bulk == 2) {
+        ok = tensor_map_2d(a.src.main, 2 * p->m1, p->n0 * p->n1 / 2, 2 * p->m1, w, &map) &&
+             tensor_map_2d(a.src.main, 2 * p->m1, p->n0 * p->n1 / 2, 2 * p->m1, w + 2, &map2);
+    }
+    if (!ok) a.bulk = 0;
+    if (a.bulk) mp = &map;
+    if (a.bulk == 2) mp2 = &map2;
+    return run_pass(p, kind, st, [&] { return col_launch(p, L, a, tiles, tw, st, mp, mp2); });
+}
+
+int run_xpass(fft3d_plan p, int kind, CLayout src, CLayout dst, int inverse, cudaStream_t st)
+{
+    int64_t tiles;
+    const ColArgs a = xpass_args(p, src, dst, inverse, &tiles);
+    return run_colpass(p, kind, a, tiles, (int)p->n0, p->tw0, st);
+}
+
+int run_ypass(fft3d_plan p, int kind, CLayout src, CLayout dst, int inverse, cudaStream_t st)
+{
+    int64_t tiles;
+    const ColArgs a = ypass_args(p, src, dst, inverse, &tiles);
+    return run_colpass(p, kind, a, tiles, (int)p->n1, p->tw1, st);
 }
 
 int check_exec(fft3d_plan p, const void *in, const void *out, bool real_in)
@@ -252,11 +349,7 @@ int forward_pipeline(fft3d_plan p, const void *in, void *out, cudaStream_t st, d
     if (p->fused) {
         rc = run_fused(p, K_R2C_ZY, z, L, 1, st);
         if (rc) return rc;
-        if (p->n0 > 1) {
-            int64_t tiles;
-            const ColArgs a = xpass_args(p, L, L, 0, &tiles);
-            rc = run_pass(p, K_R2C_X, st, [&] { return col_launch(p, (int)p->n0, a, tiles, p->tw0, st); });
-        }
+        if (p->n0 > 1) rc = run_xpass(p, K_R2C_X, L, L, 0, st);
         return rc;
     }
     rc = run_pass(p, K_R2C_Z, st, [&] {
@@ -265,18 +358,11 @@ int forward_pipeline(fft3d_plan p, const void *in, void *out, cudaStream_t st, d
     });
     if (rc) return rc;
     if (p->n1 > 1) {
-        int64_t tiles;
-        const ColArgs a = ypass_args(p, L, L, 0, &tiles);
-        rc = run_pass(p, K_R2C_Y, st, [&] { return col_launch(p, (int)p->n1, a, tiles, p->tw1, st); });
+        rc = run_ypass(p, K_R2C_Y, L, L, 0, st);
         if (rc) return rc;
     }
-    if (p->n0 > 1) {
-        int64_t tiles;
-        const ColArgs a = xpass_args(p, L, L, 0, &tiles);
-        rc = run_pass(p, K_R2C_X, st, [&] { return col_launch(p, (int)p->n0, a, tiles, p->tw0, st); });
-        if (rc) return rc;
-    }
-    return FFT3D_OK;
+    if (p->n0 > 1) rc = run_xpass(p, K_R2C_X, L, L, 0, st);
+    return rc;
 }
 
 // C2R pipeline: x -> y -> z (C2R with edge weight `we` and output scale `s`).
@@ -294,9 +380,7 @@ int inverse_pipeline(fft3d_plan p, const void *in, void *out, cudaStream_t st, d
     const CLayout dst = (inplace || overwrite_input) ? src : CLayout{out, p->nyq, 1};
     int rc;
     if (p->n0 > 1 || dst.main != src.main) {
-        int64_t tiles;
-        const ColArgs a = xpass_args(p, src, dst, 1, &tiles);
-        rc = run_pass(p, K_C2R_X, st, [&] { return col_launch(p, (int)p->n0, a, tiles, p->tw0, st); });
+        rc = run_xpass(p, K_C2R_X, src, dst, 1, st);
         if (rc) return rc;
     }
     ZArgs z;
@@ -309,9 +393,7 @@ int inverse_pipeline(fft3d_plan p, const void *in, void *out, cudaStream_t st, d
     z.scale_mid = s;
     if (p->fused) return run_fused(p, K_C2R_YZ, z, dst, 0, st);
     if (p->n1 > 1) {
-        int64_t tiles;
-        const ColArgs a = ypass_args(p, dst, dst, 1, &tiles);
-        rc = run_pass(p, K_C2R_Y, st, [&] { return col_launch(p, (int)p->n1, a, tiles, p->tw1, st); });
+        rc = run_ypass(p, K_C2R_Y, dst, dst, 1, st);
         if (rc) return rc;
     }
     return run_pass(p, K_C2R_Z, st, [&] {
@@ -410,8 +492,14 @@ int fft3d_plan_create(fft3d_plan *out, int64_t n0, int64_t n1, int64_t n2, int d
             rc = FFT3D_ERR_ALLOC;
             goto fail;
         }
+        e = cudaMalloc((void **)&p->status, 4 * sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMemset(p->status, 0, 4 * sizeof(unsigned));
+        if (e != cudaSuccess) {
+            rc = FFT3D_ERR_ALLOC;
+            goto fail;
+        }
         if (p->fused_ok) {
-            const size_t words = (size_t)(kSyncDone + n0 + 1);
+            const size_t words = (size_t)(kSyncDone + n0);
             e = cudaMalloc((void **)&p->sync, words * sizeof(unsigned));
             if (e != cudaSuccess) {
                 rc = FFT3D_ERR_ALLOC;
@@ -441,6 +529,7 @@ fail:
     if (p->tw) cudaFree(p->tw);
     if (p->nyq) cudaFree(p->nyq);
     if (p->sync) cudaFree(p->sync);
+    if (p->status) cudaFree(p->status);
     delete p;
     (void)cudaGetLastError();
     return rc;
@@ -457,8 +546,10 @@ int fft3d_plan_destroy(fft3d_plan p)
     cudaError_t e1 = p->tw ? cudaFree(p->tw) : cudaSuccess;
     cudaError_t e2 = p->nyq ? cudaFree(p->nyq) : cudaSuccess;
     cudaError_t e3 = p->sync ? cudaFree(p->sync) : cudaSuccess;
+    cudaError_t e4 = p->status ? cudaFree(p->status) : cudaSuccess;
     delete p;
-    return (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess) ? FFT3D_OK : FFT3D_ERR_CUDA;
+    return (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && e4 == cudaSuccess) ? FFT3D_OK
+                                                                                              : FFT3D_ERR_CUDA;
 }
 
 int fft3d_exec_r2c(fft3d_plan p, const void *in_real, void *out_cplx, void *stream)
@@ -573,8 +664,7 @@ int fft3d_plan_status(fft3d_plan p, int *device_error)
 {
     if (!p || !device_error) return FFT3D_ERR_NULL;
     *device_error = 0;
-    if (!p->sync) return FFT3D_OK;
-    unsigned *sticky = p->sync + kSyncDone + p->n0;
+    unsigned *sticky = p->status;
     unsigned v = 0;
     cudaError_t e = cudaMemcpy(&v, sticky, sizeof(v), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && v) e = cudaMemset(sticky, 0, sizeof(unsigned));

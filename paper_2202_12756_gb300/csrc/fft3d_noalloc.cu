@@ -131,6 +131,9 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
     char *twz = tw1 + kTableSlot;
     char *rot = twz + kTableSlot;
     void *plane = (char *)scratch + kTableBytes;
+    // device error word of the pipelined column kernel: the table slack after the
+    // last twiddle table (no table uses its final 256 bytes)
+    unsigned *err_flag = (unsigned *)((char *)scratch + kTableBytes - 256);
 
     cudaError_t e;
     if ((e = write_line_tables(f32, (int)n0, g0.E, tw0, st)) != cudaSuccess ||
@@ -156,7 +159,9 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
         a.tiles_main = tiles;
         a.tiles_per_plane = 0;
         a.nyq_in_plane = 0;
-        e = f32 ? col_launch_f32((int)n0, a, tiles, tw0, st) : col_launch_f64((int)n0, a, tiles, tw0, st);
+        a.bulk = 0;
+        a.err = err_flag;
+        e = f32 ? col_launch_f32((int)n0, a, tiles, tw0, nullptr, nullptr, st) : col_launch_f64((int)n0, a, tiles, tw0, nullptr, nullptr, st);
         if (e != cudaSuccess) return FFT3D_ERR_CUDA;
     }
     if (n1 > 1) {  // y-pass: axis 1, k2 < M tiles per plane, then the k2 = M column
@@ -171,8 +176,10 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
         a.tiles_per_plane = (m + g1.per_block - 1) / g1.per_block;
         a.tiles_main = n0 * a.tiles_per_plane;
         a.nyq_in_plane = 0;
+        a.bulk = 0;
+        a.err = err_flag;
         const int64_t tiles = a.tiles_main + (n0 + g1.per_block - 1) / g1.per_block;
-        e = f32 ? col_launch_f32((int)n1, a, tiles, tw1, st) : col_launch_f64((int)n1, a, tiles, tw1, st);
+        e = f32 ? col_launch_f32((int)n1, a, tiles, tw1, nullptr, nullptr, st) : col_launch_f64((int)n1, a, tiles, tw1, nullptr, nullptr, st);
         if (e != cudaSuccess) return FFT3D_ERR_CUDA;
     }
     ZArgs z;

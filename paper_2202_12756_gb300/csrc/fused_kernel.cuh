@@ -35,7 +35,7 @@ struct FusedArgs {
     int64_t yi;            // Y items per plane
     int64_t lag;           // planes between a plane's producers and its consumers
     int64_t n_items;       // n0 * (zi + yi)
-    unsigned *sync;        // [0] tickets, [1] launch error, [8 + p] producers done, [8 + n0] sticky error
+    unsigned *sync;        // [0] tickets, [1] launch error, [8 + p] producers done (sticky error: y.err)
     long long spin_limit;  // polls before a consumer gives up
     int inject_stall;      // test hook: consumers wait for one producer more than exists
     int forward;           // 1: R2C (Z -> Y); 0: C2R (Y -> Z)
@@ -131,7 +131,7 @@ fused_plane_kernel(FusedArgs a, const typename cvec<R>::T *__restrict__ tw_y,
                     }
                     if (++polls > a.spin_limit) {
                         atomicOr(sync + kSyncLaunchErr, 1u);
-                        atomicOr(sync + kSyncDone + a.n0, 1u);  // sticky: survives the next launch
+                        atomicOr(a.y.err, 1u);  // sticky: survives the next launch
                         abort = 1;
                         break;
                     }

@@ -2,6 +2,8 @@
 // kern_{col,z}_{f32,f64}.cu translation units.
 #pragma once
 
+#include <cstring>
+
 #include "launchers.h"
 
 namespace fft3d {
@@ -69,8 +71,11 @@ template <typename R, int L> inline void col_geom_t(PassGeom *g)
     g->per_block = W;
     g->E = E;
     g->persistent = col_pipe<R, L>() ? 1 : 0;
-    g->smem = (size_t)L * W * sizeof(typename cvec<R>::T);
-    if (col_pipe<R, L>()) g->smem += (size_t)split_rows<L>() * W * sizeof(R);
+    typedef typename cvec<R>::T C;
+    if (col_pipe<R, L>())
+        g->smem = (size_t)stage_elems<C, W, L>() * sizeof(C) + (size_t)split_rows<L>() * W * sizeof(R) + 8;
+    else
+        g->smem = (size_t)L * W * sizeof(C);
 }
 
 template <typename R, int M> inline void z_geom_t(PassGeom *g)
@@ -133,7 +138,8 @@ template <class K> inline int persistent_grid(K kernel, int threads, size_t smem
 }
 
 template <typename R, int L>
-inline cudaError_t col_launch_t(const ColArgs &a, int64_t tiles, const void *tw, cudaStream_t st)
+inline cudaError_t col_launch_t(const ColArgs &a, int64_t tiles, const void *tw, const CUtensorMap *tmap,
+                                const CUtensorMap *tmap2, cudaStream_t st)
 {
     PassGeom g;
     col_geom_t<R, L>(&g);
@@ -142,7 +148,12 @@ inline cudaError_t col_launch_t(const ColArgs &a, int64_t tiles, const void *tw,
         auto k = a.inverse ? colpass_pipe_kernel<R, L, col_E<R, L>(), col_W<R, L>(), true>
                            : colpass_pipe_kernel<R, L, col_E<R, L>(), col_W<R, L>(), false>;
         const int grid = persistent_grid(k, g.threads, g.smem, tiles);
-        k<<<grid, g.threads, g.smem, st>>>(a, (TW)tw, tiles);
+        CUtensorMap map, map2;
+        if (tmap) map = *tmap;
+        else memset(&map, 0, sizeof(map));
+        if (tmap2) map2 = *tmap2;
+        else memset(&map2, 0, sizeof(map2));
+        k<<<grid, g.threads, g.smem, st>>>(a, (TW)tw, tiles, map, map2);
     } else {
         auto k = a.inverse ? colpass_kernel<R, L, col_E<R, L>(), col_W<R, L>(), true>
                            : colpass_kernel<R, L, col_E<R, L>(), col_W<R, L>(), false>;
@@ -230,7 +241,7 @@ inline cudaError_t fused_launch_t(const FusedArgs &a, const void *tw_y, const vo
 #define FFT3D_CASE_Z_GEOM(M) case M: z_geom_t<R, M>(g); return true;
 #define FFT3D_CASE_COL_PREP(L) case L: return col_prepare_t<R, L>();
 #define FFT3D_CASE_Z_PREP(M) case M: return z_prepare_t<R, M>();
-#define FFT3D_CASE_COL_LAUNCH(L) case L: return col_launch_t<R, L>(a, tiles, tw, st);
+#define FFT3D_CASE_COL_LAUNCH(L) case L: return col_launch_t<R, L>(a, tiles, tw, tmap, tmap2, st);
 #define FFT3D_CASE_ZR2C_LAUNCH(M) case M: return zr2c_launch_t<R, M>(a, tw, rot, st);
 #define FFT3D_CASE_ZC2R_LAUNCH(M) case M: return zc2r_launch_t<R, M>(a, tw, rot, st);
 
@@ -247,6 +258,7 @@ inline cudaError_t fused_launch_t(const FusedArgs &a, const void *tw_y, const vo
         return cudaErrorInvalidValue;                                                           \
     }                                                                                           \
     cudaError_t col_launch_##SUF(int L, const ColArgs &a, int64_t tiles, const void *tw,       \
+                                 const CUtensorMap *tmap, const CUtensorMap *tmap2,             \
                                  cudaStream_t st)                                               \
     {                                                                                           \
         switch (L) { FFT3D_COL_LENGTHS(FFT3D_CASE_COL_LAUNCH) }                                 \

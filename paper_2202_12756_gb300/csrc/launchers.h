@@ -35,7 +35,7 @@ struct PassGeom {
     cudaError_t col_prepare_##SUF(int L);                                                            \
     cudaError_t z_prepare_##SUF(int M);                                                              \
     cudaError_t col_launch_##SUF(int L, const ColArgs &a, int64_t tiles, const void *tw,            \
-                                 cudaStream_t st);                                                   \
+                                 const CUtensorMap *tmap, const CUtensorMap *tmap2, cudaStream_t st);\
     cudaError_t zr2c_launch_##SUF(int M, const ZArgs &a, const void *tw, const void *rot,           \
                                   cudaStream_t st);                                                  \
     cudaError_t zc2r_launch_##SUF(int M, const ZArgs &a, const void *tw, const void *rot,           \

@@ -20,6 +20,8 @@
 //               all-to-all (Steps 2-5): no transposed copy of the array exists.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (type only)
+
 #include "line_fft.cuh"
 
 namespace fft3d {
@@ -46,6 +48,9 @@ struct ColArgs {
     int64_t tiles_main;       // tiles of the main column set
     int64_t tiles_per_plane;  // y-pass: main tiles per k0 plane
     int nyq_in_plane;         // y-pass: tiles cover k2 = 0..M of one plane (last one ragged)
+    int bulk;                 // pipelined pass, tiles t < tiles_main: 0 cp.async, 1 TMA (dense rows),
+                              // 2 TMA (y-pass rows of odd complex pitch, even / odd row maps)
+    unsigned *err;            // pipelined pass: device error flag (a stage-fill wait ran out)
 };
 
 template <typename C>
@@ -194,63 +199,194 @@ __device__ __forceinline__ void cp_async_16(void *smem, const void *gmem)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t mb, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mb), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mb, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mb), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mb, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mb), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false if it ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mb, uint32_t parity, long long limit)
+{
+    for (long long n = 0; n < limit; ++n) {
+        if (mbar_try_wait(mb, parity)) return true;
+        __nanosleep(32);
+    }
+    return false;
+}
+// TMA: copy the 2D box at (x, y) of the tensor map into this CTA's shared
+// memory (x counts reals of the innermost dimension), completing on `mb`.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mb)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(mb)
+        : "memory");
+}
+
+// rows of one TMA box of the column-tile tensor map
+constexpr int kTmaBoxRows = 256;
+
+// Staging row: W complex values (one 128-byte segment for float); in mode 2
+// the odd rows are fetched 2 complex wider, from one column before the tile.
+template <typename C, int W> __host__ __device__ constexpr int stage_row_elems() { return W; }
+template <typename C, int W, int L> __host__ __device__ constexpr int stage_elems() { return L / 2 * W + L / 2 * (W + 2); }
+
+// polls of a stage-fill wait before the kernel gives up (about 0.1 s)
+constexpr long long kStageWaitPolls = 1LL << 22;
+
 // Persistent, software-pipelined column pass.  Each block walks the tiles
 // t = blockIdx.x, blockIdx.x + gridDim.x, ...  While a tile is transformed in
 // registers, the next tile is already streaming from HBM into a shared-memory
-// staging buffer with asynchronous copies (cp.async).  Every thread stages
-// exactly the elements it will later own (rows j + i NT of its column), so a
-// thread only waits for its own copies; it issues the next tile's copies into
-// its slots after the first exchange barrier, when its reads of them have
-// completed.  The stage exchange uses a separate split (real / imaginary)
-// buffer.  Shared memory: L W complex (staging) + (L + L/32 + 1) W reals.
+// staging buffer.  Full tiles of the standard layout are fetched by one
+// thread with TMA tensor copies of 256 rows x W columns, completing on an
+// mbarrier (tensor maps over 8-byte elements, coordinates in complex units):
+//   a.bulk = 1: rows 16-byte aligned (x-pass; y-pass with an even row pitch):
+//               one map, rows (tile row 0) + b 256, dense [L][W] staging;
+//   a.bulk = 2: y-pass with an odd row pitch (N2/2 + 1 odd): every other row
+//               starts 8 bytes past a 16-byte boundary, but a pair of rows is
+//               a multiple of 16 bytes, so the plane is a [N1/2][2 (M+1)]
+//               tensor: even rows come from column c0 (W wide), odd rows from
+//               column c0 + M of the pair (W + 2 wide, i.e. one column early),
+//               into [L/2][W] + [L/2][W+2] staging.
+// Other tiles are staged element by element with cp.async, each thread
+// copying exactly the elements it will own.  The next tile's copies are issued after the first exchange
+// barrier, when every thread's reads of the staging buffer have completed.
+// The stage exchange uses a separate split (real / imaginary) buffer.  A
+// tile wait that runs out raises *a.err and the block leaves after a second
+// bounded wait.  Shared memory: L (W + 1) complex (staging) + (L + L/32 + 1) W
+// reals + 8 bytes (mbarrier).
 template <typename R, int L, int E, int W, bool INV>
 __global__ void __launch_bounds__(W *(L / E), (W * (L / E) >= 512 ? 1 : 512 / (W * (L / E))))
-colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64_t ntiles)
+colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64_t ntiles,
+                    const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap2)
 {
     typedef typename cvec<R>::T C;
     constexpr int NT = L / E;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int RSE = stage_row_elems<C, W>();
+    static_assert(L % (2 * kTmaBoxRows) == 0 && NT % 2 == 0 && (RSE * sizeof(C)) % 16 == 0, "staging layout");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     C *stage = (C *)smem_raw;
-    ColSplitEx<R, W> ex{(R *)(stage + L * W), 0};
+    C *stage_odd = stage + L / 2 * W;  // mode 2: odd rows, W + 2 wide
+    R *exbuf = (R *)(stage + stage_elems<C, W, L>());
+    uint64_t *mbar = (uint64_t *)(exbuf + split_rows<L>() * W);
     const int c = threadIdx.x % W;
     const int j = threadIdx.x / W;
-    ex.c = c;
+    ColSplitEx<R, W> ex{exbuf, c};
+    const uint32_t mb = smem_u32(mbar);
+    if (threadIdx.x == 0) {
+        mbar_init(mb, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
 
-    auto prefetch = [&](const C *sp, int64_t ss) {
-        const C *sj = sp + (int64_t)j * ss;
-        const int64_t sstep = (int64_t)NT * ss;
+    // Start staging tile tt; returns its mode (0 cp.async, 1 or 2 TMA).
+    auto fill = [&](int64_t tt, const C *sp, int64_t ss) -> int {
+        const int mode = tt < a.tiles_main ? a.bulk : 0;
+        if (mode) {
+            if (threadIdx.x == 0) {
+                // order the block's earlier reads of the buffer before the async-proxy writes
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                if (mode == 1) {
+                    mbar_arrive_expect_tx(mb, (unsigned)(L * W * sizeof(C)));
+                    int x, y0;
+                    if (a.axis == 0) {  // [N0][N1 (M+1)]: the tile's flat columns, all rows
+                        x = (int)(tt * W);
+                        y0 = 0;
+                    } else {            // [N0 N1][M+1]: plane k0, columns c0..
+                        const int64_t k0 = tt / a.tiles_per_plane;
+                        x = (int)((tt - k0 * a.tiles_per_plane) * W);
+                        y0 = (int)(k0 * a.n1);
+                    }
 #pragma unroll
-        for (int i = 0; i < E; ++i) {
-            C *dst = stage + (j + i * NT) * W + c;
-            if (sizeof(C) == 8) cp_async_8(dst, sj + i * sstep);
-            else cp_async_16(dst, sj + i * sstep);
+                    for (int b = 0; b < L / kTmaBoxRows; ++b)
+                        tma_load_2d(smem_u32(stage + b * kTmaBoxRows * W), &tmap, x, y0 + b * kTmaBoxRows, mb);
+                } else {
+                    mbar_arrive_expect_tx(mb, (unsigned)(L / 2 * (2 * W + 2) * sizeof(C)));
+                    const int64_t k0 = tt / a.tiles_per_plane;
+                    const int c0 = (int)((tt - k0 * a.tiles_per_plane) * W);
+                    const int y0 = (int)(k0 * (a.n1 / 2));
+#pragma unroll
+                    for (int b = 0; b < L / 2 / kTmaBoxRows; ++b) {
+                        tma_load_2d(smem_u32(stage + b * kTmaBoxRows * W), &tmap, c0, y0 + b * kTmaBoxRows, mb);
+                        tma_load_2d(smem_u32(stage_odd + b * kTmaBoxRows * (W + 2)), &tmap2, c0 + (int)a.m,
+                                    y0 + b * kTmaBoxRows, mb);
+                    }
+                }
+            }
+        } else {
+            const C *sj = sp + (int64_t)j * ss;
+            const int64_t sstep = (int64_t)NT * ss;
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                C *dst = stage + (j + i * NT) * RSE + c;
+                if (sizeof(C) == 8) cp_async_8(dst, sj + i * sstep);
+                else cp_async_16(dst, sj + i * sstep);
+            }
+            cp_async_commit();
         }
+        return mode;
     };
 
     int64_t t = blockIdx.x;
     C *sp = nullptr, *dp = nullptr;
     int64_t ss = 0, ds = 0;
     bool valid = t < ntiles && col_decode<C, W>(a, t, c, sp, ss, dp, ds);
-    if (t < ntiles) prefetch(sp, ss);
-    cp_async_commit();
+    int mode = t < ntiles ? fill(t, sp, ss) : 0;
     while (t < ntiles) {
         const int64_t tn = t + gridDim.x;
         C *spn = nullptr, *dpn = nullptr;
         int64_t ssn = 0, dsn = 0;
         const bool validn = tn < ntiles && col_decode<C, W>(a, tn, c, spn, ssn, dpn, dsn);
 
-        cp_async_wait_all();  // this thread's copies of tile t have landed
-        C v[E];
-#pragma unroll
-        for (int i = 0; i < E; ++i) {
-            v[i] = stage[(j + i * NT) * W + c];
-            if (INV) v[i].y = -v[i].y;
+        if (mode) {
+            const bool ok = mbar_wait_bounded(mb, phase, kStageWaitPolls);
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) atomicOr(a.err, 1u);
+                mbar_wait_bounded(mb, phase, kStageWaitPolls);  // copies still in flight
+                return;
+            }
+            phase ^= 1u;
+        } else {
+            cp_async_wait_all();  // this thread's copies of tile t have landed
         }
-        // Stage the next tile into the same slots once these reads are
-        // complete, i.e. after the first exchange barrier.
+        C v[E];
+        if (mode == 2) {
+            // rows j + i NT (NT even) share the parity of j
+            const C *base = (j & 1) ? stage_odd + (j >> 1) * (W + 2) + c + 1 : stage + (j >> 1) * W + c;
+            const int step = (j & 1) ? (NT / 2) * (W + 2) : (NT / 2) * W;
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                v[i] = base[i * step];
+                if (INV) v[i].y = -v[i].y;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                v[i] = stage[(j + i * NT) * RSE + c];
+                if (INV) v[i].y = -v[i].y;
+            }
+        }
+        int moden = 0;
         auto next = [&]() {
-            if (tn < ntiles) prefetch(spn, ssn);
-            cp_async_commit();
+            if (tn < ntiles) moden = fill(tn, spn, ssn);
         };
         line_fft<R, L, E>(v, j, tw, ex, next);
         if (valid) {
@@ -265,6 +401,7 @@ colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
         }
         t = tn;
         valid = validn;
+        mode = moden;
         sp = spn;
         ss = ssn;
         dp = dpn;

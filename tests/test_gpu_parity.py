@@ -209,3 +209,13 @@ def test_host_resident_field(name):
     plan.c2r_overwrite(X, host_out)
     torch.cuda.synchronize()
     assert rel_l2(host_out.numpy(), f) <= TOL[name]
+
+
+@pytest.mark.parametrize("shape", [(4, 1024, 64), (6, 2048, 64), (1024, 16, 32), (2048, 16, 32), (1024, 1024, 32)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_tma_staged_column_passes(shape):
+    """Float column passes of 1024 / 2048 points stage full tiles with TMA
+    tensor copies: one map over aligned rows (x-pass), or even / odd row maps
+    when the y-pass row pitch (N2/2 + 1 complex) is odd.  Both layouts."""
+    for inplace in (False, True):
+        check_pair(shape, "f32", inplace, seed=9)
