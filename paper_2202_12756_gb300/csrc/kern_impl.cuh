@@ -73,7 +73,8 @@ template <typename R, int L> inline void col_geom_t(PassGeom *g)
     g->persistent = col_pipe<R, L>() ? 1 : 0;
     typedef typename cvec<R>::T C;
     if (col_pipe<R, L>())
-        g->smem = (size_t)stage_elems<C, W, L>() * sizeof(C) + (size_t)split_rows<L>() * W * sizeof(R) + 8;
+        g->smem = (size_t)stage_elems<C, W, L>() * sizeof(C) + (size_t)split_rows<L>() * W * sizeof(R) + 16 +
+                  (size_t)line_tw_size(L, E) * sizeof(C);
     else
         g->smem = (size_t)L * W * sizeof(C);
 }

@@ -3,7 +3,8 @@
 //
 // All butterflies compute the forward DFT y[k] = sum_n a[n] exp(-2 pi i n k / R)
 // (Eq. 1's sign).  Inverse transforms reuse them through
-// IDFT(x) = conj(DFT(conj(x))), applied when a pass loads and stores.
+// IDFT(x) = conj(DFT(conj(x))) = swap(DFT(swap(x))), swap exchanging the real
+// and imaginary parts, applied when a pass loads and stores.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -38,6 +39,8 @@ template <typename C> __device__ __forceinline__ C cmulc(C a, C b)
 // -i * a
 template <typename C> __device__ __forceinline__ C cmul_mi(C a) { return cmake<C>(a.y, -a.x); }
 template <typename C> __device__ __forceinline__ C cconj(C a) { return cmake<C>(a.x, -a.y); }
+// (re, im) -> (im, re); swap(DFT(swap(x))) is the unnormalised inverse DFT
+template <typename C> __device__ __forceinline__ C cswap(C a) { return cmake<C>(a.y, a.x); }
 template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return cmake<C>(a.x * s, a.y * s); }
 
 // cos(pi/8), sin(pi/8), sqrt(1/2), sqrt(3)/2
@@ -221,7 +224,15 @@ template <typename C> struct Dft<32, C> {
 // y[(b / Ns) Ns R + k + m Ns]; they are left in the input slots and the
 // exchange (for every stage but the last) moves them to their owners.  The
 // last stage's output slots coincide with its input slots (natural order).
-template <typename R, int L, int E, int S>
+// Twiddle read: read-only global path, or a plain load when the table was
+// copied to shared memory (TWS).
+template <bool TWS, typename C> __device__ __forceinline__ C tw_read(const C *__restrict__ tw, int i)
+{
+    if constexpr (TWS) return tw[i];
+    else return __ldg(tw + i);
+}
+
+template <typename R, int L, int E, int S, bool TWS = false>
 __device__ __forceinline__ void line_stage_compute(typename cvec<R>::T *v, int j,
                                                    const typename cvec<R>::T *__restrict__ tw)
 {
@@ -241,7 +252,7 @@ __device__ __forceinline__ void line_stage_compute(typename cvec<R>::T *v, int j
         for (int m = 0; m < RS; ++m) t[m] = v[q + m * Q];
         if (S > 0) {
 #pragma unroll
-            for (int m = 1; m < RS; ++m) t[m] = cmul(t[m], __ldg(tw + TWO + (m - 1) * NS + k));
+            for (int m = 1; m < RS; ++m) t[m] = cmul(t[m], tw_read<TWS>(tw, TWO + (m - 1) * NS + k));
         }
         Dft<RS, C>::run(t);
 #pragma unroll
@@ -326,33 +337,34 @@ __device__ __forceinline__ void line_exchange(typename cvec<R>::T *v, int j, Ex 
     }
 }
 
-template <typename R, int L, int E, int S, class Ex, class Hook>
+template <typename R, int L, int E, int S, bool TWS, class Ex, class Hook>
 __device__ __forceinline__ void line_stages_from(typename cvec<R>::T *v, int j,
                                                  const typename cvec<R>::T *__restrict__ tw, Ex &ex,
                                                  const Hook &hook)
 {
     if constexpr (S < line_nstages(L, E)) {
-        line_stage_compute<R, L, E, S>(v, j, tw);
+        line_stage_compute<R, L, E, S, TWS>(v, j, tw);
         if constexpr (S + 1 < line_nstages(L, E)) {
             if constexpr (S == 0) line_exchange<R, L, E, S>(v, j, ex, hook);
             else line_exchange<R, L, E, S>(v, j, ex, NoHook());
         } else if constexpr (S == 0) {
             hook();
         }
-        line_stages_from<R, L, E, S + 1>(v, j, tw, ex, hook);
+        line_stages_from<R, L, E, S + 1, TWS>(v, j, tw, ex, hook);
     }
 }
 
 // Forward FFT of a line held as v[i] = x[j + i NT]; result in the same slots.
 // `hook` runs once after the first exchange barrier (or after the only stage).
-template <typename R, int L, int E, class Ex, class Hook = NoHook>
+// TWS: `tw` points to a copy of the twiddle table in shared memory.
+template <typename R, int L, int E, bool TWS = false, class Ex, class Hook = NoHook>
 __device__ __forceinline__ void line_fft(typename cvec<R>::T *v, int j,
                                          const typename cvec<R>::T *__restrict__ tw, Ex &ex,
                                          const Hook &hook = Hook())
 {
     static_assert(line_plan_valid(L, E), "invalid line plan");
     if constexpr (line_nstages(L, E) == 0) hook();
-    line_stages_from<R, L, E, 0>(v, j, tw, ex, hook);
+    line_stages_from<R, L, E, 0, TWS>(v, j, tw, ex, hook);
 }
 
 }  // namespace fft3d

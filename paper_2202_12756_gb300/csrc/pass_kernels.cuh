@@ -44,7 +44,7 @@ struct ColArgs {
     CLayout src, dst;
     int64_t n0, n1, m;        // grid N0, N1 and M = N2 / 2
     int axis;                 // 0: rows are k0 (x-pass); 1: rows are k1 (y-pass)
-    int inverse;              // 1: exp(+...) via conj in / conj out
+    int inverse;              // 1: exp(+...) via swapped re / im in and out
     int64_t tiles_main;       // tiles of the main column set
     int64_t tiles_per_plane;  // y-pass: main tiles per k0 plane
     int nyq_in_plane;         // y-pass: tiles cover k2 = 0..M of one plane (last one ragged)
@@ -159,7 +159,7 @@ __device__ __forceinline__ void col_tile(const ColArgs &a, int64_t tile, unsigne
 #pragma unroll
     for (int i = 0; i < E; ++i) {
         v[i] = CG ? load_cg(sj + i * sstep) : sj[i * sstep];
-        if (INV) v[i].y = -v[i].y;
+        if (INV) v[i] = cswap(v[i]);
     }
     ColEx<C, W> ex{(C *)smem, c};
     line_fft<R, L, E>(v, j, tw, ex);
@@ -169,7 +169,7 @@ __device__ __forceinline__ void col_tile(const ColArgs &a, int64_t tile, unsigne
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             C o = v[i];
-            if (INV) o.y = -o.y;
+            if (INV) o = cswap(o);
             dj[i * dstep] = o;
         }
     }
@@ -271,7 +271,8 @@ constexpr long long kStageWaitPolls = 1LL << 22;
 // The stage exchange uses a separate split (real / imaginary) buffer.  A
 // tile wait that runs out raises *a.err and the block leaves after a second
 // bounded wait.  Shared memory: L (W + 1) complex (staging) + (L + L/32 + 1) W
-// reals + 8 bytes (mbarrier).
+// reals + 16 bytes (mbarrier) + the twiddle table, which every block copies
+// once (a thread's twiddles are the same in every tile).
 template <typename R, int L, int E, int W, bool INV>
 __global__ void __launch_bounds__(W *(L / E), (W * (L / E) >= 512 ? 1 : 512 / (W * (L / E))))
 colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64_t ntiles,
@@ -286,6 +287,9 @@ colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
     C *stage_odd = stage + L / 2 * W;  // mode 2: odd rows, W + 2 wide
     R *exbuf = (R *)(stage + stage_elems<C, W, L>());
     uint64_t *mbar = (uint64_t *)(exbuf + split_rows<L>() * W);
+    C *tws = (C *)(mbar + 2);  // the block's copy of the twiddle table
+    constexpr int NTW = line_tw_size(L, E);
+    for (int i = threadIdx.x; i < NTW; i += blockDim.x) tws[i] = __ldg(tw + i);
     const int c = threadIdx.x % W;
     const int j = threadIdx.x / W;
     ColSplitEx<R, W> ex{exbuf, c};
@@ -375,27 +379,27 @@ colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
 #pragma unroll
             for (int i = 0; i < E; ++i) {
                 v[i] = base[i * step];
-                if (INV) v[i].y = -v[i].y;
+                if (INV) v[i] = cswap(v[i]);
             }
         } else {
 #pragma unroll
             for (int i = 0; i < E; ++i) {
                 v[i] = stage[(j + i * NT) * RSE + c];
-                if (INV) v[i].y = -v[i].y;
+                if (INV) v[i] = cswap(v[i]);
             }
         }
         int moden = 0;
         auto next = [&]() {
             if (tn < ntiles) moden = fill(tn, spn, ssn);
         };
-        line_fft<R, L, E>(v, j, tw, ex, next);
+        line_fft<R, L, E, true>(v, j, tws, ex, next);
         if (valid) {
             C *dj = dp + (int64_t)j * ds;
             const int64_t dstep = (int64_t)NT * ds;
 #pragma unroll
             for (int i = 0; i < E; ++i) {
                 C o = v[i];
-                if (INV) o.y = -o.y;
+                if (INV) o = cswap(o);
                 dj[i * dstep] = o;
             }
         }
