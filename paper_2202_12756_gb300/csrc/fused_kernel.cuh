@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(W *(N1 / line_E(N1)), MINB)
 fused_plane_kernel(FusedArgs a, const typename cvec<R>::T *__restrict__ tw_y,
                    const typename cvec<R>::T *__restrict__ tw_z, const typename cvec<R>::T *__restrict__ rot)
 {
-    static_assert(W * (N1 / line_E(N1)) == LPB * (M / line_E(M)), "Y and Z items need the same block");
+    static_assert(W * (N1 / line_E(N1)) == LPB * (M / z_E<R, M>()), "Y and Z items need the same block");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int64_t s_ticket;
     __shared__ int s_abort;
@@ -145,8 +145,8 @@ fused_plane_kernel(FusedArgs a, const typename cvec<R>::T *__restrict__ tw_y,
 
         if (z_item) {
             const int64_t line0 = plane * a.y.n1 + idx * LPB;
-            if (a.forward) zr2c_lines<R, M, line_E(M), LPB>(a.z, line0, smem_raw, tw_z, rot);
-            else zc2r_lines<R, M, line_E(M), LPB, true>(a.z, line0, smem_raw, tw_z, rot);
+            if (a.forward) zr2c_lines<R, M, z_E<R, M>(), LPB>(a.z, line0, smem_raw, tw_z, rot);
+            else zc2r_lines<R, M, z_E<R, M>(), LPB, true>(a.z, line0, smem_raw, tw_z, rot);
         } else {
             const int64_t tile = plane * a.yi + idx;
             if (a.forward) col_tile<R, N1, line_E(N1), W, true, false>(a.y, tile, smem_raw, tw_y);

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstring>
+#include <mutex>
 
 #include "launchers.h"
 
@@ -58,9 +59,9 @@ template <typename R, int L> __host__ __device__ constexpr int col_W()
 }
 
 // Lines per block of a z pass: about 256 threads, and at least one warp.
-template <int M> __host__ __device__ constexpr int z_LPB()
+template <typename R, int M> __host__ __device__ constexpr int z_LPB()
 {
-    return line_NT(M) >= FFT3D_Z_THREADS ? 1 : FFT3D_Z_THREADS / line_NT(M);
+    return M / z_E<R, M>() >= FFT3D_Z_THREADS ? 1 : FFT3D_Z_THREADS / (M / z_E<R, M>());
 }
 
 template <typename R, int L> inline void col_geom_t(PassGeom *g)
@@ -73,18 +74,17 @@ template <typename R, int L> inline void col_geom_t(PassGeom *g)
     g->persistent = col_pipe<R, L>() ? 1 : 0;
     typedef typename cvec<R>::T C;
     if (col_pipe<R, L>())
-        g->smem = (size_t)stage_elems<C, W, L>() * sizeof(C) + (size_t)split_rows<L>() * W * sizeof(R) + 16 +
-                  (size_t)line_tw_size(L, E) * sizeof(C);
+        g->smem = pipe_smem_bytes<R, L, E, W>();
     else
         g->smem = (size_t)L * W * sizeof(C);
 }
 
 template <typename R, int M> inline void z_geom_t(PassGeom *g)
 {
-    constexpr int LPB = z_LPB<M>();
-    g->threads = LPB * line_NT(M);
+    constexpr int LPB = z_LPB<R, M>();
+    g->threads = LPB * (M / z_E<R, M>());
     g->per_block = LPB;
-    g->E = line_E(M);
+    g->E = z_E<R, M>();
     g->persistent = 0;
     g->smem = (size_t)LPB * zline_smem_elems<M>() * sizeof(typename cvec<R>::T);
 }
@@ -113,29 +113,48 @@ template <typename R, int M> inline cudaError_t z_prepare_t()
 {
     PassGeom g;
     z_geom_t<R, M>(&g);
-    cudaError_t e = cudaFuncSetAttribute(zpass_r2c_kernel<R, M, line_E(M), z_LPB<M>()>,
+    cudaError_t e = cudaFuncSetAttribute(zpass_r2c_kernel<R, M, z_E<R, M>(), z_LPB<R, M>()>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(zpass_c2r_kernel<R, M, line_E(M), z_LPB<M>()>,
+    return cudaFuncSetAttribute(zpass_c2r_kernel<R, M, z_E<R, M>(), z_LPB<R, M>()>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
 }
 
-// Resident blocks of a persistent kernel on the current device (cached per
-// device for each kernel instantiation).
-template <class K> inline int persistent_grid(K kernel, int threads, size_t smem, int64_t tiles)
+// Resident blocks of a persistent kernel on the current device, cached per
+// (kernel, device), capped at the blocks that get work: `items` work items
+// taken `per_block_items` at a time.
+template <class K>
+inline int persistent_grid(K kernel, int threads, size_t smem, int64_t items, int per_block_items = 1)
 {
-    static int cache[128];
+    struct Entry {
+        const void *k;
+        int dev;
+        int blocks;
+    };
+    static Entry cache[64];
+    static std::mutex mu;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) dev = 0;
-    int per_dev = cache[dev];
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    int per_dev = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (const Entry &e : cache)
+            if (e.k == (const void *)kernel && e.dev == dev) per_dev = e.blocks;
+    }
     if (per_dev <= 0) {
         int sms = 0, nb = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem);
         per_dev = (sms > 0 ? sms : 1) * (nb > 0 ? nb : 1);
-        cache[dev] = per_dev;
+        std::lock_guard<std::mutex> lock(mu);
+        for (Entry &e : cache)
+            if (e.k == nullptr) {
+                e = Entry{(const void *)kernel, dev, per_dev};
+                break;
+            }
     }
-    return (int)(tiles < per_dev ? tiles : per_dev);
+    const int64_t need = (items + per_block_items - 1) / per_block_items;
+    return (int)(need < per_dev ? need : per_dev);
 }
 
 template <typename R, int L>
@@ -169,7 +188,7 @@ inline cudaError_t zr2c_launch_t(const ZArgs &a, const void *tw, const void *rot
     PassGeom g;
     z_geom_t<R, M>(&g);
     const int64_t blocks = (a.nlines + g.per_block - 1) / g.per_block;
-    zpass_r2c_kernel<R, M, line_E(M), z_LPB<M>()><<<(unsigned)blocks, g.threads, g.smem, st>>>(
+    zpass_r2c_kernel<R, M, z_E<R, M>(), z_LPB<R, M>()><<<(unsigned)blocks, g.threads, g.smem, st>>>(
         a, (const typename cvec<R>::T *)tw, (const typename cvec<R>::T *)rot);
     return cudaGetLastError();
 }
@@ -180,7 +199,7 @@ inline cudaError_t zc2r_launch_t(const ZArgs &a, const void *tw, const void *rot
     PassGeom g;
     z_geom_t<R, M>(&g);
     const int64_t blocks = (a.nlines + g.per_block - 1) / g.per_block;
-    zpass_c2r_kernel<R, M, line_E(M), z_LPB<M>()><<<(unsigned)blocks, g.threads, g.smem, st>>>(
+    zpass_c2r_kernel<R, M, z_E<R, M>(), z_LPB<R, M>()><<<(unsigned)blocks, g.threads, g.smem, st>>>(
         a, (const typename cvec<R>::T *)tw, (const typename cvec<R>::T *)rot);
     return cudaGetLastError();
 }
@@ -191,8 +210,8 @@ inline cudaError_t zc2r_launch_t(const ZArgs &a, const void *tw, const void *rot
 template <int N1, int M> struct FusedShape {
     static constexpr int T = 512;
     static constexpr int W = T / (N1 / line_E(N1));
-    static constexpr int LPB = T / (M / line_E(M));
-    static constexpr int MINB = (line_E(N1) <= 16 && line_E(M) <= 16) ? 2 : 1;
+    static constexpr int LPB = T / (M / z_E<float, M>());
+    static constexpr int MINB = (line_E(N1) <= 16 && z_E<float, M>() <= 16) ? 2 : 1;
 };
 
 template <typename R, int N1, int M> inline void fused_geom_t(PassGeom *g, int *z_lines)

@@ -232,6 +232,22 @@ template <bool TWS, typename C> __device__ __forceinline__ C tw_read(const C *__
     else return __ldg(tw + i);
 }
 
+// Compile-time loop: f(IntC<I>()) for I = B .. N-1.
+template <int I> struct IntC {
+    static constexpr int value = I;
+};
+template <int B, int N, class F> __device__ __forceinline__ void static_for(const F &f)
+{
+    if constexpr (B < N) {
+        f(IntC<B>());
+        static_for<B + 1, N>(f);
+    }
+}
+
+#ifndef FFT3D_TWCONST
+#define FFT3D_TWCONST 1
+#endif
+
 template <typename R, int L, int E, int S, bool TWS = false>
 __device__ __forceinline__ void line_stage_compute(typename cvec<R>::T *v, int j,
                                                    const typename cvec<R>::T *__restrict__ tw)
@@ -243,20 +259,48 @@ __device__ __forceinline__ void line_stage_compute(typename cvec<R>::T *v, int j
     constexpr int Q = E / RS;
     constexpr int TWO = line_tw_offset(L, E, S);
     static_assert(E % RS == 0, "radix must divide the elements per thread");
+    if constexpr (FFT3D_TWCONST && sizeof(R) == 4 && S > 0 && Q > 1 && NS % NT == 0) {
+        // Butterfly q of this thread has k = j + c_q, c_q = (q NT) mod Ns, so
+        // W^{m k} = W^{m j} W^{m c_q}: the R - 1 factors W^{m j} come from the
+        // table once, the W^{m c_q} (W = exp(-2 pi i / (Ns R))) are constants.
+        C base[RS];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const int b = j + q * NT;
-        const int k = b % NS;
-        C t[RS];
+        for (int m = 1; m < RS; ++m) base[m] = tw_read<TWS>(tw, TWO + (m - 1) * NS + j);
+        static_for<0, Q>([&](auto QI) {
+            constexpr int q = decltype(QI)::value;
+            constexpr int cq = (q * NT) % NS;
+            C t[RS];
 #pragma unroll
-        for (int m = 0; m < RS; ++m) t[m] = v[q + m * Q];
-        if (S > 0) {
+            for (int m = 0; m < RS; ++m) t[m] = v[q + m * Q];
+            static_for<1, RS>([&](auto MI) {
+                constexpr int m = decltype(MI)::value;
+                if constexpr (cq == 0) {
+                    t[m] = cmul(t[m], base[m]);
+                } else {
+                    constexpr CtCosSin w = ct_cossin_pi(-2LL * m * cq, (long long)NS * RS);
+                    t[m] = cmul(t[m], cmul(base[m], cmake<C>(R(w.c), R(w.s))));
+                }
+            });
+            Dft<RS, C>::run(t);
 #pragma unroll
-            for (int m = 1; m < RS; ++m) t[m] = cmul(t[m], tw_read<TWS>(tw, TWO + (m - 1) * NS + k));
+            for (int m = 0; m < RS; ++m) v[q + m * Q] = t[m];
+        });
+    } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int b = j + q * NT;
+            const int k = b % NS;
+            C t[RS];
+#pragma unroll
+            for (int m = 0; m < RS; ++m) t[m] = v[q + m * Q];
+            if (S > 0) {
+#pragma unroll
+                for (int m = 1; m < RS; ++m) t[m] = cmul(t[m], tw_read<TWS>(tw, TWO + (m - 1) * NS + k));
+            }
+            Dft<RS, C>::run(t);
+#pragma unroll
+            for (int m = 0; m < RS; ++m) v[q + m * Q] = t[m];
         }
-        Dft<RS, C>::run(t);
-#pragma unroll
-        for (int m = 0; m < RS; ++m) v[q + m * Q] = t[m];
     }
 }
 

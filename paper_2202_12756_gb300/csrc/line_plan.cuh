@@ -78,6 +78,52 @@ __host__ __device__ constexpr int line_ns(int L, int E, int s)
     return p;
 }
 
+// cos(pi p / q) and sin(pi p / q) evaluated by the compiler, for twiddle
+// factors that are the same in every thread: the angle is reduced exactly
+// (integer arithmetic) to [0, pi/4] by the symmetries of sin and cos, then
+// both Maclaurin series are summed to the x^27 term in double (the remainder
+// is below 1e-30 there).  Used only in constant expressions.
+struct CtCosSin {
+    double c, s;
+};
+
+__host__ __device__ constexpr CtCosSin ct_maclaurin(double x)
+{
+    const double x2 = x * x;
+    double s = x, ts = x, c = 1.0, tc = 1.0;
+    for (int k = 1; k <= 13; ++k) {
+        ts *= -x2 / (double)((2 * k) * (2 * k + 1));
+        tc *= -x2 / (double)((2 * k - 1) * (2 * k));
+        s += ts;
+        c += tc;
+    }
+    return CtCosSin{c, s};
+}
+
+__host__ __device__ constexpr CtCosSin ct_cossin_pi(long long p, long long q)
+{
+    long long n = p % (2 * q), d = q;
+    if (n < 0) n += 2 * q;
+    bool neg_c = false, neg_s = false, swap = false;
+    if (n >= d) {  // theta - pi
+        n -= d;
+        neg_c = !neg_c;
+        neg_s = !neg_s;
+    }
+    if (2 * n > d) {  // pi - theta
+        n = d - n;
+        neg_c = !neg_c;
+    }
+    if (4 * n > d) {  // pi/2 - theta = pi (d - 2n) / 2d
+        n = d - 2 * n;
+        d = 2 * d;
+        swap = true;
+    }
+    const CtCosSin r = ct_maclaurin(3.141592653589793238 * (double)n / (double)d);
+    const double c = swap ? r.s : r.c, s = swap ? r.c : r.s;
+    return CtCosSin{neg_c ? -c : c, neg_s ? -s : s};
+}
+
 // Stage s > 0 reads twiddles W_{Ns R}^{m k} (m = 1..R-1, k < Ns) from
 // table[offset(s) + (m - 1) * Ns + k]; stage 0 needs none (all k = 0).
 __host__ __device__ constexpr int line_tw_offset(int L, int E, int s)

@@ -251,6 +251,14 @@ template <typename C, int W, int L> __host__ __device__ constexpr int stage_elem
 // polls of a stage-fill wait before the kernel gives up (about 0.1 s)
 constexpr long long kStageWaitPolls = 1LL << 22;
 
+// Shared memory of the pipelined column pass: staging (L/2 W + L/2 (W + 2)
+// complex), the split exchange buffer, the mbarrier, then the twiddle table.
+template <typename R, int L, int E, int W> __host__ __device__ constexpr size_t pipe_smem_bytes()
+{
+    return (size_t)stage_elems<typename cvec<R>::T, W, L>() * sizeof(typename cvec<R>::T) +
+           (size_t)split_rows<L>() * W * sizeof(R) + 16 + (size_t)line_tw_size(L, E) * sizeof(typename cvec<R>::T);
+}
+
 // Persistent, software-pipelined column pass.  Each block walks the tiles
 // t = blockIdx.x, blockIdx.x + gridDim.x, ...  While a tile is transformed in
 // registers, the next tile is already streaming from HBM into a shared-memory
@@ -266,13 +274,14 @@ constexpr long long kStageWaitPolls = 1LL << 22;
 //               column c0 + M of the pair (W + 2 wide, i.e. one column early),
 //               into [L/2][W] + [L/2][W+2] staging.
 // Other tiles are staged element by element with cp.async, each thread
-// copying exactly the elements it will own.  The next tile's copies are issued after the first exchange
-// barrier, when every thread's reads of the staging buffer have completed.
-// The stage exchange uses a separate split (real / imaginary) buffer.  A
-// tile wait that runs out raises *a.err and the block leaves after a second
-// bounded wait.  Shared memory: L (W + 1) complex (staging) + (L + L/32 + 1) W
-// reals + 16 bytes (mbarrier) + the twiddle table, which every block copies
-// once (a thread's twiddles are the same in every tile).
+// copying exactly the elements it will own.  The next tile's copies are
+// issued after the first exchange barrier, when every thread's reads of the
+// staging buffer have completed.  The stage exchange uses a separate split
+// (real / imaginary) buffer.  A tile wait that runs out raises *a.err and the
+// block leaves after a second bounded wait.  The twiddle table is copied to
+// shared memory once per block (a thread's twiddles are the same in every
+// tile).  The tile is W = 16 float2 columns: 128-byte row segments, which
+// HBM serves at about twice the rate of 64-byte ones at this row stride.
 template <typename R, int L, int E, int W, bool INV>
 __global__ void __launch_bounds__(W *(L / E), (W * (L / E) >= 512 ? 1 : 512 / (W * (L / E))))
 colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64_t ntiles,
@@ -282,8 +291,8 @@ colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
     constexpr int NT = L / E;
     constexpr int RSE = stage_row_elems<C, W>();
     static_assert(L % (2 * kTmaBoxRows) == 0 && NT % 2 == 0 && (RSE * sizeof(C)) % 16 == 0, "staging layout");
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    C *stage = (C *)smem_raw;
+    extern __shared__ __align__(1024) unsigned char pipe_smem_raw[];
+    C *stage = (C *)pipe_smem_raw;
     C *stage_odd = stage + L / 2 * W;  // mode 2: odd rows, W + 2 wide
     R *exbuf = (R *)(stage + stage_elems<C, W, L>());
     uint64_t *mbar = (uint64_t *)(exbuf + split_rows<L>() * W);
@@ -349,6 +358,10 @@ colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
         return mode;
     };
 
+    // Tiles t = blockIdx.x + q gridDim.x: at any moment the blocks work on
+    // neighbouring tiles, whose rows share DRAM pages (measured on GB300:
+    // giving each block runs of 2, 4 or 8 consecutive tiles instead slows
+    // the y-pass by 15, 27 and 45%).
     int64_t t = blockIdx.x;
     C *sp = nullptr, *dp = nullptr;
     int64_t ss = 0, ds = 0;
@@ -425,6 +438,12 @@ struct ZArgs {
     double scale_mid;     // r2c: factor on the other outputs;    c2r: output factor
 };
 
+// Elements per thread of a z-pass line: the default plan of the length (16,
+// or 24 for 3 * 2^k; radix 16 first).  32 elements (radix 32 first, one
+// exchange fewer) doubles the registers of a thread and, measured on GB300
+// at M = 512, halves the resident warps and runs 25% slower.
+template <typename R, int M> __host__ __device__ constexpr int z_E() { return line_E(M); }
+
 // Per-line shared-memory exchange with one padding slot every 16 elements,
 // which makes the stride-16 writes of a radix-16 first stage conflict-free.
 // Indices arrive padded (i + (i >> 4), see pad_row).
@@ -443,8 +462,37 @@ template <typename C, int NT> struct LineEx {
 
 template <int M> __host__ __device__ constexpr int zline_smem_elems() { return (M + 1) + ((M + 1) >> 4) + 1; }
 
+#ifndef FFT3D_ROTCONST
+#define FFT3D_ROTCONST 1
+#endif
+
+// Rotation factor rot[k] = exp(-2 pi i k / 2M) of slot i (k = j + i NT).
+// Float lines load rot[j] once and multiply by the slot's constant
+// exp(-i pi i / E) (NT / 2M = 1 / 2E); double lines load every factor.
+template <typename R, int E, int I>
+__device__ __forceinline__ typename cvec<R>::T z_rot(typename cvec<R>::T rot_j,
+                                                     const typename cvec<R>::T *__restrict__ rot, int k)
+{
+    typedef typename cvec<R>::T C;
+    if constexpr (FFT3D_ROTCONST && sizeof(R) == 4) {
+        if constexpr (I == 0) {
+            return rot_j;
+        } else {
+            constexpr CtCosSin w = ct_cossin_pi(-(long long)I, E);
+            return cmul(rot_j, cmake<C>(R(w.c), R(w.s)));
+        }
+    } else {
+        return __ldg(rot + k);
+    }
+}
+
 // LPB lines starting at line0, NT = M / E threads per line.  R2C: load the
 // real line as M complex pairs, M-point FFT, Hermitian post-process.
+// Thread j holds Z[j + i NT]; the partner Z[M - k] of k = j + i NT is slot
+// E - 1 - i of lane NT - j (j > 0) or this lane's slot (E - i) mod E (j = 0),
+// so when a float line fits a warp the post-process takes it by shuffle
+// (double lines, bound by FP64 arithmetic, keep the shared-memory exchange
+// and its lower register count).
 template <typename R, int M, int E, int LPB>
 __device__ __forceinline__ void zr2c_lines(const ZArgs &a, int64_t line0, unsigned char *smem,
                                            const typename cvec<R>::T *__restrict__ tw,
@@ -452,6 +500,7 @@ __device__ __forceinline__ void zr2c_lines(const ZArgs &a, int64_t line0, unsign
 {
     typedef typename cvec<R>::T C;
     constexpr int NT = M / E;
+    constexpr int P = LineEx<C, NT>::kPadShift;
     const int lt = threadIdx.x / NT;
     const int j = threadIdx.x % NT;
     const int64_t line = line0 + lt;
@@ -462,28 +511,45 @@ __device__ __forceinline__ void zr2c_lines(const ZArgs &a, int64_t line0, unsign
     C v[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) v[i] = active ? in[j + i * NT] : cmake<C>(R(0), R(0));
+    C rot_j = cmake<C>(R(1), R(0));
+    if constexpr (FFT3D_ROTCONST && sizeof(R) == 4) rot_j = __ldg(rot + j);
 
     line_fft<R, M, E>(v, j, tw, ex);
 
-    // Hermitian post-process: needs Z[k] and Z[M - k] together
-    constexpr bool LR = pad_linear_reads<4>(NT);
-    constexpr bool LREV = NT % 16 == 0;  // M - j - i NT stays linear in i
-#pragma unroll
-    for (int i = 0; i < E; ++i) ex.put(pad_row<4, LR>(j, i * NT), v[i]);
-    ex.sync();
     C *out = (C *)a.cplx.main + (active ? line : 0) * (M + 1);
     const R se = R(a.scale_edge), sm = R(a.scale_mid);
-#pragma unroll
-    for (int i = 0; i < E; ++i) {
-        const int k = j + i * NT;
-        const C z = ex.get(pad_row<4, LR>(j, i * NT));
-        const C zm = ex.get(pad_row<4, LREV>(M - j, -i * NT));  // Z[M - k]; k = 0 reads index M
-        const C zc = cconj((i == 0 && j == 0) ? z : zm);          // Z[(M - k) mod M]
-        const C s = cadd(z, zc);                         // 2 E[k]
-        const C d = cmul(__ldg(rot + k), csub(z, zc));   // 2i W^k O[k]
-        // X[k] = (s - i d) / 2
+    // X[k] = (s - i d) / 2 from z = Z[k] and zm = Z[(M - k) mod M]
+    auto emit = [&](int k, C z, C zm, C r) {
+        const C zc = cconj(zm);
+        const C s = cadd(z, zc);          // 2 E[k]
+        const C d = cmul(r, csub(z, zc));  // 2i W^k O[k]
         const R f = R(0.5) * (k == 0 ? se : sm);
         if (active) out[k] = cmake<C>(f * (s.x + d.y), f * (s.y - d.x));
+    };
+    if constexpr (NT <= 32 && sizeof(R) == 4) {
+        const int src = (NT - j) & (NT - 1);
+        static_for<0, E>([&](auto II) {
+            constexpr int i = decltype(II)::value;
+            const int k = j + i * NT;
+            C zp;
+            zp.x = __shfl_sync(0xffffffffu, v[E - 1 - i].x, src, NT);
+            zp.y = __shfl_sync(0xffffffffu, v[E - 1 - i].y, src, NT);
+            const C zm = (j == 0) ? v[(E - i) % E] : zp;
+            emit(k, v[i], zm, z_rot<R, E, i>(rot_j, rot, k));
+        });
+    } else {
+        constexpr bool LR = pad_linear_reads<P>(NT);
+        constexpr bool LREV = NT % (1 << P) == 0;  // M - j - i NT stays linear in i
+#pragma unroll
+        for (int i = 0; i < E; ++i) ex.put(pad_row<P, LR>(j, i * NT), v[i]);
+        ex.sync();
+        static_for<0, E>([&](auto II) {
+            constexpr int i = decltype(II)::value;
+            const int k = j + i * NT;
+            const C z = ex.get(pad_row<P, LR>(j, i * NT));
+            const C zm = ex.get(pad_row<P, LREV>(M - j, -i * NT));  // Z[M - k]; k = 0 reads index M
+            emit(k, z, (i == 0 && j == 0) ? z : zm, z_rot<R, E, i>(rot_j, rot, k));
+        });
     }
     if (active && j == 0) {
         // X[M] = E[0] - O[0] = Re Z[0] - Im Z[0]
@@ -493,6 +559,8 @@ __device__ __forceinline__ void zr2c_lines(const ZArgs &a, int64_t line0, unsign
 
 // C2R of LPB lines: Hermitian pre-process, M-point inverse FFT, unpack into
 // 2M reals with the output scale.  CG selects L2-only loads of the spectrum.
+// The partner X[M - k] comes by shuffle as in zr2c_lines (lane 0 pairs k = 0
+// with X[M], which it loads itself).
 template <typename R, int M, int E, int LPB, bool CG>
 __device__ __forceinline__ void zc2r_lines(const ZArgs &a, int64_t line0, unsigned char *smem,
                                            const typename cvec<R>::T *__restrict__ tw,
@@ -500,6 +568,7 @@ __device__ __forceinline__ void zc2r_lines(const ZArgs &a, int64_t line0, unsign
 {
     typedef typename cvec<R>::T C;
     constexpr int NT = M / E;
+    constexpr int P = LineEx<C, NT>::kPadShift;
     const int lt = threadIdx.x / NT;
     const int j = threadIdx.x % NT;
     const int64_t line = line0 + lt;
@@ -516,35 +585,58 @@ __device__ __forceinline__ void zc2r_lines(const ZArgs &a, int64_t line0, unsign
         src = (const C *)a.cplx.main + l * (M + 1);
         nyq = src + M;
     }
-    constexpr bool LR = pad_linear_reads<4>(NT);
-    constexpr bool LREV = NT % 16 == 0;
     C v[E];
 #pragma unroll
     for (int i = 0; i < E; ++i)
         v[i] = active ? (CG ? load_cg(src + j + i * NT) : src[j + i * NT]) : cmake<C>(R(0), R(0));
-#pragma unroll
-    for (int i = 0; i < E; ++i) ex.put(pad_row<4, LR>(j, i * NT), v[i]);
-    if (j == 0) ex.put(pad_row<4, true>(M, 0), active ? (CG ? load_cg(nyq) : *nyq) : cmake<C>(R(0), R(0)));
-    ex.sync();
+    C rot_j = cmake<C>(R(1), R(0));
+    if constexpr (FFT3D_ROTCONST && sizeof(R) == 4) rot_j = __ldg(rot + j);
 
     const R we = R(a.scale_edge);
-#pragma unroll
-    for (int i = 0; i < E; ++i) {
-        const int k = j + i * NT;
-        C x = ex.get(pad_row<4, LR>(j, i * NT));
-        C y = ex.get(pad_row<4, LREV>(M - j, -i * NT));  // X[M - k]; k = 0 pairs with X[M]
+    // conj(Z[k]), Z = E + i O, from x = X[k] and y = X[M - k]
+    auto pre = [&](int k, C x, C y, C r) -> C {
         if (k == 0) {
             // only the real parts of the k2 = 0 and k2 = M entries enter
             x = cmake<C>(we * x.x, R(0));
             y = cmake<C>(we * y.x, R(0));
         }
         const C yc = cconj(y);
-        const C e = cadd(x, yc);                         // E[k] (times 2)
-        const C o = cmulc(csub(x, yc), __ldg(rot + k));  // O[k] (times 2)
-        // Z = E + i O, kept conjugated for the inverse transform
-        v[i] = cmake<C>(e.x - o.y, -(e.y + o.x));
+        const C e = cadd(x, yc);               // E[k] (times 2)
+        const C o = cmulc(csub(x, yc), r);     // O[k] (times 2)
+        return cmake<C>(e.x - o.y, -(e.y + o.x));
+    };
+    if constexpr (NT <= 32 && sizeof(R) == 4) {
+        const C xm = (active && j == 0) ? (CG ? load_cg(nyq) : *nyq) : cmake<C>(R(0), R(0));
+        const int srcl = (NT - j) & (NT - 1);
+        C pv[E];
+        static_for<0, E>([&](auto II) {
+            constexpr int i = decltype(II)::value;
+            C p;
+            p.x = __shfl_sync(0xffffffffu, v[E - 1 - i].x, srcl, NT);
+            p.y = __shfl_sync(0xffffffffu, v[E - 1 - i].y, srcl, NT);
+            pv[i] = (j == 0) ? (i == 0 ? xm : v[(E - i) % E]) : p;
+        });
+        static_for<0, E>([&](auto II) {
+            constexpr int i = decltype(II)::value;
+            const int k = j + i * NT;
+            v[i] = pre(k, v[i], pv[i], z_rot<R, E, i>(rot_j, rot, k));
+        });
+    } else {
+        constexpr bool LR = pad_linear_reads<P>(NT);
+        constexpr bool LREV = NT % (1 << P) == 0;
+#pragma unroll
+        for (int i = 0; i < E; ++i) ex.put(pad_row<P, LR>(j, i * NT), v[i]);
+        if (j == 0) ex.put(pad_row<P, true>(M, 0), active ? (CG ? load_cg(nyq) : *nyq) : cmake<C>(R(0), R(0)));
+        ex.sync();
+        static_for<0, E>([&](auto II) {
+            constexpr int i = decltype(II)::value;
+            const int k = j + i * NT;
+            const C x = ex.get(pad_row<P, LR>(j, i * NT));
+            const C y = ex.get(pad_row<P, LREV>(M - j, -i * NT));  // X[M - k]; k = 0 pairs with X[M]
+            v[i] = pre(k, x, y, z_rot<R, E, i>(rot_j, rot, k));
+        });
+        ex.sync();
     }
-    ex.sync();
 
     line_fft<R, M, E>(v, j, tw, ex);
 
