@@ -235,6 +235,35 @@ def cpu_baseline(budget_s=12.0, n=256):
             "sample": f"{pairs} FP64 R2C+C2R pairs of a {n}^3 uniform field ({dt:.1f} s)"}
 
 
+def torch_fft_reference(x_padded, grid, dev, steps=10, warmup=3):
+    """torch.fft.rfftn + irfftn (cuFFT) on the same field and GPU, out of
+    place: a timed reference point only; the library never calls it."""
+    import torch
+    n0, n1, n = grid
+    x = x_padded[..., :n].contiguous()
+    stream = torch.cuda.current_stream(dev)
+
+    def pair():
+        return torch.fft.irfftn(torch.fft.rfftn(x), s=(n0, n1, n))
+
+    for _ in range(warmup):
+        pair()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        pair()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    del x
+    torch.cuda.empty_cache()
+    return {"ms_per_step": round(ms, 3), "gflops": round(pair_flops(n0, n1, n) / (ms * 1e-3) / 1e9, 1),
+            "steps": steps, "what": "torch.fft.rfftn + torch.fft.irfftn (cuFFT), out of place, same FP32 field "
+                                    "and GPU; timed reference point, not called by the library"}
+
+
 def round_trip_error(plan, host_in, host_out):
     """Relative L2 error of the last e2e step's round trip (host tensors)."""
     d = (host_out.double() - host_in.double()).norm() / host_in.double().norm()
@@ -298,6 +327,9 @@ def run_ours(args):
     flops = pair_flops(n0, n1, n)
     bytes_pair = 2 * pass_bytes(n0, n1, n, 4)
     value = flops * world / (t_step * 1e-3) / 1e9
+
+    # ---- reference point: cuFFT through torch.fft on the same field (rank 0)
+    torch_ref = torch_fft_reference(buf32, grid, dev) if rank == 0 else None
 
     # ---- FP64 pair (same field)
     steps64 = max(2, args.steps // 10)
@@ -366,6 +398,9 @@ def run_ours(args):
         "clocks": clk,
         "peak_source": peaks["src"],
     }
+    if torch_ref is not None:
+        torch_ref["ours_speedup"] = round(torch_ref["ms_per_step"] / t_step, 2)
+        line["torch_fft_reference"] = torch_ref
     rt = round_trip_error(plan32, host_in, host_out)
     line["fp32_round_trip_rel_l2"] = rt
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -78,6 +78,22 @@ enum fft3d_status {
  */
 int fft3d_plan_create(fft3d_plan *plan, int64_t n0, int64_t n1, int64_t n2, int dtype);
 
+/*
+ * Batched plan: every exec call transforms `batch` fields of N0 x N1 x N2
+ * stored one after another (real [batch][N0][N1][N2] dense or
+ * [batch][N0][N1][2(N2/2+1)] padded; complex [batch][N0][N1][N2/2+1]), with
+ * one launch per pass for all of them, e.g. the three velocity components of
+ * the pseudo-spectral turbulence solvers that motivate the paper (Sec. 1),
+ * or several fields in flight as in the batched GPU-FFT it compares with
+ * (Sec. 5).  Each field is transformed exactly as by a plan of batch 1 (and
+ * normalised by 1/(N0 N1 N2)); the fields never mix.  The scratch plane of
+ * the out-of-place inverse grows to batch*N0*N1 elements.  batch must be
+ * >= 1 with batch*N0*N1 <= 2^31, else FFT3D_ERR_SIZE.  The opt-in fused
+ * plane pass is not offered for batch > 1.  fft3d_plan_create(p, ...) is
+ * fft3d_plan_create_batched(p, 1, ...).
+ */
+int fft3d_plan_create_batched(fft3d_plan *plan, int64_t batch, int64_t n0, int64_t n1, int64_t n2, int dtype);
+
 /* Release the plan and its device memory.  NULL is accepted (no-op).
  * The caller must make sure no stream still runs work of this plan. */
 int fft3d_plan_destroy(fft3d_plan plan);

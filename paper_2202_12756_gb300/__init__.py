@@ -46,7 +46,7 @@ EXPORTED = (
     "fft3d_plan_last_error", "fft3d_supported_length", "fft3d_plan_set_profiling",
     "fft3d_plan_profile_read", "fft3d_plan_launch_count", "fft3d_exec_c2r_noalloc",
     "fft3d_plan_status", "fft3d_plan_set_debug", "fft3d_plan_info", "fft3d_plan_set_fused",
-    "fft3d_exec_c2r_overwrite",
+    "fft3d_exec_c2r_overwrite", "fft3d_plan_create_batched",
 )
 
 
@@ -72,6 +72,7 @@ def _declare(lib):
     P = ctypes.c_void_p
     I64 = ctypes.c_int64
     lib.fft3d_plan_create.argtypes = [ctypes.POINTER(P), I64, I64, I64, ctypes.c_int]
+    lib.fft3d_plan_create_batched.argtypes = [ctypes.POINTER(P), I64, I64, I64, I64, ctypes.c_int]
     lib.fft3d_plan_destroy.argtypes = [P]
     for f in ("fft3d_exec_r2c", "fft3d_exec_c2r", "fft3d_exec_r2c_adjoint", "fft3d_exec_c2r_adjoint",
               "fft3d_exec_c2r_overwrite"):
@@ -134,6 +135,13 @@ def _check(rc, where, plan=None):
 def fft3d_plan_create(n0, n1, n2, dtype):
     h = ctypes.c_void_p()
     _check(load_library().fft3d_plan_create(ctypes.byref(h), n0, n1, n2, dtype), "fft3d_plan_create")
+    return h.value
+
+
+def fft3d_plan_create_batched(batch, n0, n1, n2, dtype):
+    h = ctypes.c_void_p()
+    _check(load_library().fft3d_plan_create_batched(ctypes.byref(h), batch, n0, n1, n2, dtype),
+           "fft3d_plan_create_batched")
     return h.value
 
 
@@ -250,18 +258,22 @@ def real_of(complex_dtype):
 
 
 class Plan:
-    """An fft3d plan for one (N0, N1, N2, dtype) on one CUDA device."""
+    """An fft3d plan for one (N0, N1, N2, dtype) on one CUDA device.  With
+    batch > 1 every call transforms `batch` fields: tensors carry a leading
+    batch dimension ([B, N0, N1, N2] real, [B, N0, N1, N2/2+1] complex)."""
 
-    def __init__(self, shape, dtype, device=None):
+    def __init__(self, shape, dtype, device=None, batch=1):
         torch = _torch()
         self.shape = tuple(int(s) for s in shape)
+        self.batch = int(batch)
+        self.lead = (self.batch,) if self.batch > 1 else ()
         self.real_dtype = dtype
         self.complex_dtype = complex_of(dtype)
         self.device = torch.device(device if device is not None else "cuda", )
         if self.device.index is None:
             self.device = torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(self.device):
-            self.handle = fft3d_plan_create(*self.shape, _dtype_code(dtype))
+            self.handle = fft3d_plan_create_batched(self.batch, *self.shape, _dtype_code(dtype))
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -275,7 +287,11 @@ class Plan:
     @property
     def half_shape(self):
         n0, n1, n2 = self.shape
-        return (n0, n1, n2 // 2 + 1)
+        return self.lead + (n0, n1, n2 // 2 + 1)
+
+    @property
+    def real_shape(self):
+        return self.lead + self.shape
 
     def _stream(self):
         return _torch().cuda.current_stream(self.device).cuda_stream
@@ -286,7 +302,7 @@ class Plan:
             fn(self.handle, src.data_ptr(), dst.data_ptr(), self._stream())
 
     def empty_real(self):
-        return _torch().empty(self.shape, dtype=self.real_dtype, device=self.device)
+        return _torch().empty(self.real_shape, dtype=self.real_dtype, device=self.device)
 
     def empty_complex(self):
         return _torch().empty(self.half_shape, dtype=self.complex_dtype, device=self.device)
@@ -294,11 +310,12 @@ class Plan:
     def empty_padded(self):
         """Real buffer with rows padded to 2 (N2/2 + 1): the in-place layout."""
         n0, n1, n2 = self.shape
-        return _torch().empty((n0, n1, 2 * (n2 // 2 + 1)), dtype=self.real_dtype, device=self.device)
+        return _torch().empty(self.lead + (n0, n1, 2 * (n2 // 2 + 1)), dtype=self.real_dtype,
+                              device=self.device)
 
     def _check_real(self, t, padded=False, host_ok=False):
         n0, n1, n2 = self.shape
-        want = (n0, n1, 2 * (n2 // 2 + 1)) if padded else self.shape
+        want = self.lead + ((n0, n1, 2 * (n2 // 2 + 1)) if padded else self.shape)
         where_ok = t.device == self.device or (host_ok and t.device.type == "cpu" and t.is_pinned())
         if t.dtype != self.real_dtype or tuple(t.shape) != want or not t.is_contiguous() or not where_ok:
             raise FFT3DError(FFT3D_ERR_ARG, "real tensor", f"need contiguous {want} {self.real_dtype} on {self.device}")
@@ -389,18 +406,28 @@ _plans = {}
 _plans_lock = threading.Lock()
 
 
-def get_plan(shape, dtype, device):
+def get_plan(shape, dtype, device, batch=1):
     torch = _torch()
     device = torch.device(device)
     if device.index is None:
         device = torch.device("cuda", torch.cuda.current_device())
-    key = (tuple(int(s) for s in shape), dtype, device.index)
+    key = (tuple(int(s) for s in shape), dtype, device.index, int(batch))
     with _plans_lock:
         p = _plans.get(key)
         if p is None:
-            p = Plan(shape, dtype, device)
+            p = Plan(shape, dtype, device, batch)
             _plans[key] = p
     return p
+
+
+def _split_batch(shape):
+    """(batch, field shape) of a 3D shape or a 4D [B, N0, N1, N2] shape."""
+    shape = tuple(int(s) for s in shape)
+    if len(shape) == 4:
+        return shape[0], shape[1:]
+    if len(shape) == 3:
+        return 1, shape
+    raise FFT3DError(FFT3D_ERR_ARG, "shape", f"need (N0, N1, N2) or (B, N0, N1, N2), got {shape}")
 
 
 def _make_autograd():
@@ -409,7 +436,8 @@ def _make_autograd():
     class RFFT3(torch.autograd.Function):
         @staticmethod
         def forward(ctx, x):
-            plan = get_plan(x.shape, x.dtype, x.device)
+            b, shape = _split_batch(x.shape)
+            plan = get_plan(shape, x.dtype, x.device, b)
             ctx.plan = plan
             return plan.r2c(x.contiguous())
 
@@ -420,7 +448,8 @@ def _make_autograd():
     class IRFFT3(torch.autograd.Function):
         @staticmethod
         def forward(ctx, X, shape):
-            plan = get_plan(shape, real_of(X.dtype), X.device)
+            b, shape = _split_batch(shape)
+            plan = get_plan(shape, real_of(X.dtype), X.device, b)
             ctx.plan = plan
             return plan.c2r(X.contiguous())
 
@@ -435,7 +464,8 @@ _autograd = None
 
 
 def rfft3(x):
-    """Forward R2C (Eq. 1) of a real [N0][N1][N2] CUDA tensor; differentiable."""
+    """Forward R2C (Eq. 1) of a real [N0][N1][N2] CUDA tensor, or of each field
+    of a [B][N0][N1][N2] batch; differentiable."""
     global _autograd
     if _autograd is None:
         _autograd = _make_autograd()
@@ -443,7 +473,8 @@ def rfft3(x):
 
 
 def irfft3(X, shape):
-    """Normalised inverse C2R (Eq. 2 and 1/N^3) to real `shape`; differentiable."""
+    """Normalised inverse C2R (Eq. 2 and 1/N^3) to real `shape` ((N0, N1, N2),
+    or (B, N0, N1, N2) for a batch of fields); differentiable."""
     global _autograd
     if _autograd is None:
         _autograd = _make_autograd()

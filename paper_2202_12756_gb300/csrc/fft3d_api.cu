@@ -47,6 +47,8 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct fft3d_plan_s {
     int64_t n0, n1, n2, m, m1;
+    int64_t batch;        // fields per exec call, stored one after another
+    int64_t nb0;          // batch * n0: planes of all fields
     int dtype;
     int device;
     size_t rsize, csize;  // bytes of one real / one complex element
@@ -91,7 +93,7 @@ int set_err(fft3d_plan p, int status, const char *what, cudaError_t e = cudaSucc
 
 double pass_bytes(const fft3d_plan_s *p, int kind)
 {
-    const double lines = (double)p->n0 * (double)p->n1;
+    const double lines = (double)p->nb0 * (double)p->n1;
     const double cplx = lines * (double)p->m1 * (double)p->csize;
     const double real = lines * (double)p->n2 * (double)p->rsize;
     return (kind == K_R2C_Z || kind == K_C2R_Z || kind == K_R2C_ZY || kind == K_C2R_YZ) ? cplx + real
@@ -201,22 +203,23 @@ ColArgs ypass_args(const fft3d_plan_s *p, CLayout src, CLayout dst, int inverse,
     ColArgs a;
     a.src = src;
     a.dst = dst;
-    a.n0 = p->n0;
+    a.n0 = p->nb0;  // the planes of all fields
     a.n1 = p->n1;
     a.m = p->m;
     a.axis = 1;
     a.inverse = inverse;
     const int64_t w = p->g1.per_block;
     a.tiles_per_plane = (p->m + w - 1) / w;
-    a.tiles_main = p->n0 * a.tiles_per_plane;
+    a.tiles_main = p->nb0 * a.tiles_per_plane;
     a.nyq_in_plane = 0;
     a.bulk = bulk_mode(p, src, 1, w);
     a.err = p->status;
-    *tiles = a.tiles_main + (p->n0 + w - 1) / w;
+    a.tiles_per_field = 1;
+    *tiles = a.tiles_main + (p->nb0 + w - 1) / w;
     return a;
 }
 
-// x-pass (axis 0) tiles: W consecutive flat (k1, k2) columns each.
+// x-pass (axis 0) tiles: W consecutive flat (k1, k2) columns of one field.
 ColArgs xpass_args(const fft3d_plan_s *p, CLayout src, CLayout dst, int inverse, int64_t *tiles)
 {
     ColArgs a;
@@ -228,7 +231,8 @@ ColArgs xpass_args(const fft3d_plan_s *p, CLayout src, CLayout dst, int inverse,
     a.axis = 0;
     a.inverse = inverse;
     const int64_t w = p->g0.per_block;
-    *tiles = (p->n1 * p->m1 + w - 1) / w;
+    a.tiles_per_field = (p->n1 * p->m1 + w - 1) / w;
+    *tiles = p->batch * a.tiles_per_field;
     a.tiles_main = *tiles;
     a.tiles_per_plane = 0;
     a.nyq_in_plane = 0;
@@ -258,6 +262,7 @@ int run_fused(fft3d_plan p, int kind, const ZArgs &z, CLayout ylayout, int forwa
     f.y.nyq_in_plane = 1;
     f.y.bulk = 0;
     f.y.err = p->status;
+    f.y.tiles_per_field = 1;
     f.n0 = p->n0;
     f.zi = p->n1 / p->fz_lines;
 #ifndef FFT3D_FUSED_LAG
@@ -283,12 +288,12 @@ int run_colpass(fft3d_plan p, int kind, ColArgs a, int64_t tiles, int L, const v
     const int w = (int)(a.axis == 0 ? p->g0.per_block : p->g1.per_block);
     bool ok = true;
     if (a.bulk == 1 && a.axis == 0) {
-        ok = tensor_map_2d(a.src.main, p->n1 * p->m1, p->n0, p->n1 * p->m1, w, &map);
+        ok = tensor_map_2d(a.src.main, p->n1 * p->m1, p->nb0, p->n1 * p->m1, w, &map);
     } else if (a.bulk == 1) {
-        ok = tensor_map_2d(a.src.main, p->m1, p->n0 * p->n1, p->m1, w, &map);
+        ok = tensor_map_2d(a.src.main, p->m1, p->nb0 * p->n1, p->m1, w, &map);
     } else if (a.bulk == 2) {
-        ok = tensor_map_2d(a.src.main, 2 * p->m1, p->n0 * p->n1 / 2, 2 * p->m1, w, &map) &&
-             tensor_map_2d(a.src.main, 2 * p->m1, p->n0 * p->n1 / 2, 2 * p->m1, w + 2, &map2);
+        ok = tensor_map_2d(a.src.main, 2 * p->m1, p->nb0 * p->n1 / 2, 2 * p->m1, w, &map) &&
+             tensor_map_2d(a.src.main, 2 * p->m1, p->nb0 * p->n1 / 2, 2 * p->m1, w + 2, &map2);
     }
     if (!ok) a.bulk = 0;
     if (a.bulk) mp = &map;
@@ -321,7 +326,7 @@ int check_exec(fft3d_plan p, const void *in, const void *out, bool real_in)
     if (((uintptr_t)in % p->csize) != 0 || ((uintptr_t)out % p->csize) != 0)
         return set_err(p, FFT3D_ERR_ALIGN, "data pointer not aligned to one complex element");
     if (in != out) {
-        const size_t lines = (size_t)p->n0 * (size_t)p->n1;
+        const size_t lines = (size_t)p->nb0 * (size_t)p->n1;
         const size_t rbytes = lines * (size_t)p->n2 * p->rsize;
         const size_t cbytes = lines * (size_t)p->m1 * p->csize;
         const size_t ib = real_in ? rbytes : cbytes;
@@ -342,7 +347,7 @@ int forward_pipeline(fft3d_plan p, const void *in, void *out, cudaStream_t st, d
     z.real_out = nullptr;
     z.real_pitch = (in == out) ? 2 * p->m1 : p->n2;
     z.cplx = L;
-    z.nlines = p->n0 * p->n1;
+    z.nlines = p->nb0 * p->n1;
     z.scale_edge = se;
     z.scale_mid = sm;
     int rc;
@@ -388,7 +393,7 @@ int inverse_pipeline(fft3d_plan p, const void *in, void *out, cudaStream_t st, d
     z.real_out = out;
     z.real_pitch = inplace ? 2 * p->m1 : p->n2;
     z.cplx = dst;
-    z.nlines = p->n0 * p->n1;
+    z.nlines = p->nb0 * p->n1;
     z.scale_edge = we;
     z.scale_mid = s;
     if (p->fused) return run_fused(p, K_C2R_YZ, z, dst, 0, st);
@@ -428,13 +433,22 @@ int fft3d_supported_length(int64_t n, int axis)
 
 int fft3d_plan_create(fft3d_plan *out, int64_t n0, int64_t n1, int64_t n2, int dtype)
 {
+    return fft3d_plan_create_batched(out, 1, n0, n1, n2, dtype);
+}
+
+int fft3d_plan_create_batched(fft3d_plan *out, int64_t batch, int64_t n0, int64_t n1, int64_t n2, int dtype)
+{
     if (!out) return FFT3D_ERR_NULL;
     *out = nullptr;
     if (dtype != FFT3D_F32 && dtype != FFT3D_F64) return FFT3D_ERR_DTYPE;
     if (!fft3d_supported_length(n0, 0) || !fft3d_supported_length(n1, 1) || !fft3d_supported_length(n2, 2))
         return FFT3D_ERR_SIZE;
+    // every plane-row index (batch * n0 * n1) must fit the kernels' 32-bit TMA coordinates
+    if (batch < 1 || batch > ((int64_t)1 << 31) / (n0 * n1)) return FFT3D_ERR_SIZE;
     fft3d_plan p = new (std::nothrow) fft3d_plan_s();
     if (!p) return FFT3D_ERR_ALLOC;
+    p->batch = batch;
+    p->nb0 = batch * n0;
     p->n0 = n0;
     p->n1 = n1;
     p->n2 = n2;
@@ -458,7 +472,8 @@ int fft3d_plan_create(fft3d_plan *out, int64_t n0, int64_t n1, int64_t n2, int d
         goto fail;
     }
     p->spin_limit = kDefaultSpinLimit;
-    p->fused_ok = f32 && fused_geom_f32((int)n1, (int)p->m, &p->gf, &p->fz_lines) && n1 % p->fz_lines == 0;
+    p->fused_ok = f32 && batch == 1 && fused_geom_f32((int)n1, (int)p->m, &p->gf, &p->fz_lines) &&
+                  n1 % p->fz_lines == 0;
     p->fused = 0;  // opt-in: see fft3d_plan_set_fused
 
     {
@@ -487,7 +502,7 @@ int fft3d_plan_create(fft3d_plan *out, int64_t n0, int64_t n1, int64_t n2, int d
             rc = FFT3D_ERR_CUDA;
             goto fail;
         }
-        e = cudaMalloc(&p->nyq, (size_t)n0 * (size_t)n1 * p->csize);
+        e = cudaMalloc(&p->nyq, (size_t)p->nb0 * (size_t)n1 * p->csize);
         if (e != cudaSuccess) {
             rc = FFT3D_ERR_ALLOC;
             goto fail;

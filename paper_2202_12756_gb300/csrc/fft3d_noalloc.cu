@@ -157,6 +157,7 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
         a.inverse = 1;
         const int64_t tiles = (n1 * m1 + g0.per_block - 1) / g0.per_block;
         a.tiles_main = tiles;
+        a.tiles_per_field = tiles;
         a.tiles_per_plane = 0;
         a.nyq_in_plane = 0;
         a.bulk = 0;
@@ -178,6 +179,7 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
         a.nyq_in_plane = 0;
         a.bulk = 0;
         a.err = err_flag;
+        a.tiles_per_field = 1;
         const int64_t tiles = a.tiles_main + (n0 + g1.per_block - 1) / g1.per_block;
         e = f32 ? col_launch_f32((int)n1, a, tiles, tw1, nullptr, nullptr, st) : col_launch_f64((int)n1, a, tiles, tw1, nullptr, nullptr, st);
         if (e != cudaSuccess) return FFT3D_ERR_CUDA;

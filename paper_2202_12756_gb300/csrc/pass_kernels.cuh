@@ -51,6 +51,7 @@ struct ColArgs {
     int bulk;                 // pipelined pass, tiles t < tiles_main: 0 cp.async, 1 TMA (dense rows),
                               // 2 TMA (y-pass rows of odd complex pitch, even / odd row maps)
     unsigned *err;            // pipelined pass: device error flag (a stage-fill wait ran out)
+    int64_t tiles_per_field;  // x-pass: tiles of one field; field b's columns start at row k0 = b n0
 };
 
 template <typename C>
@@ -95,9 +96,11 @@ __device__ __forceinline__ bool col_decode(const ColArgs &a, int64_t t, int c, C
     bool valid;
     if (a.axis == 0) {
         const int64_t total = a.n1 * (a.m + 1);
-        int64_t f = t * W + c;  // flat (k1, k2) index
+        const int64_t b = (uint32_t)t / (uint32_t)a.tiles_per_field;  // field of a batched plan (t < 2^32)
+        int64_t f = (t - b * a.tiles_per_field) * W + c;  // flat (k1, k2) index
         valid = f < total;
         f = valid ? f : total - 1;
+        k0 = b * a.n0;
         k1 = f / (a.m + 1);
         k2 = f - k1 * (a.m + 1);
     } else if (a.nyq_in_plane) {
@@ -248,6 +251,12 @@ constexpr int kTmaBoxRows = 256;
 template <typename C, int W> __host__ __device__ constexpr int stage_row_elems() { return W; }
 template <typename C, int W, int L> __host__ __device__ constexpr int stage_elems() { return L / 2 * W + L / 2 * (W + 2); }
 
+// Stage the next tile as soon as the current one is in registers (one extra
+// barrier per tile), instead of after the first exchange barrier.
+#ifndef FFT3D_PIPE_EARLY_PREFETCH
+#define FFT3D_PIPE_EARLY_PREFETCH 0
+#endif
+
 // polls of a stage-fill wait before the kernel gives up (about 0.1 s)
 constexpr long long kStageWaitPolls = 1LL << 22;
 
@@ -282,6 +291,10 @@ template <typename R, int L, int E, int W> __host__ __device__ constexpr size_t 
 // shared memory once per block (a thread's twiddles are the same in every
 // tile).  The tile is W = 16 float2 columns: 128-byte row segments, which
 // HBM serves at about twice the rate of 64-byte ones at this row stride.
+// Measured on GB300, two alternatives were slower: exchanging through the
+// staging buffer itself (so the next tile's copies start only after the
+// exchange) by 35-40%, and waiting for the next tile before storing this one
+// (stores interleaved with the next tile's staging reads) by 9-25%.
 template <typename R, int L, int E, int W, bool INV>
 __global__ void __launch_bounds__(W *(L / E), (W * (L / E) >= 512 ? 1 : 512 / (W * (L / E))))
 colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64_t ntiles,
@@ -320,9 +333,10 @@ colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
                 if (mode == 1) {
                     mbar_arrive_expect_tx(mb, (unsigned)(L * W * sizeof(C)));
                     int x, y0;
-                    if (a.axis == 0) {  // [N0][N1 (M+1)]: the tile's flat columns, all rows
-                        x = (int)(tt * W);
-                        y0 = 0;
+                    if (a.axis == 0) {  // [B N0][N1 (M+1)]: the tile's flat columns, its field's rows
+                        const int64_t b = (uint32_t)tt / (uint32_t)a.tiles_per_field;
+                        x = (int)((tt - b * a.tiles_per_field) * W);
+                        y0 = (int)(b * a.n0);
                     } else {            // [N0 N1][M+1]: plane k0, columns c0..
                         const int64_t k0 = tt / a.tiles_per_plane;
                         x = (int)((tt - k0 * a.tiles_per_plane) * W);
@@ -405,7 +419,14 @@ colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
         auto next = [&]() {
             if (tn < ntiles) moden = fill(tn, spn, ssn);
         };
+#if FFT3D_PIPE_EARLY_PREFETCH
+        // every thread has its elements of tile t in registers: stage tile tn now
+        __syncthreads();
+        next();
+        line_fft<R, L, E, true>(v, j, tws, ex);
+#else
         line_fft<R, L, E, true>(v, j, tws, ex, next);
+#endif
         if (valid) {
             C *dj = dp + (int64_t)j * ds;
             const int64_t dstep = (int64_t)NT * ds;

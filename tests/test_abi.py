@@ -74,6 +74,17 @@ def test_plan_create_rejects_before_touching_cuda(lib):
     assert e.value.status == fft3d.FFT3D_ERR_SIZE
 
 
+def test_batched_plan_create_rejects_before_touching_cuda(lib):
+    h = ctypes.c_void_p(1234)
+    create = lib.fft3d_plan_create_batched
+    for batch in (0, -3, (1 << 31) // (1024 * 1024) + 1):
+        assert create(ctypes.byref(h), batch, 1024, 1024, 64, fft3d.FFT3D_F32) == fft3d.FFT3D_ERR_SIZE
+        assert h.value is None
+    assert create(ctypes.byref(h), 2, 8, 8, 7, fft3d.FFT3D_F32) == fft3d.FFT3D_ERR_SIZE
+    assert create(ctypes.byref(h), 2, 8, 8, 8, 9) == fft3d.FFT3D_ERR_DTYPE
+    assert create(None, 2, 8, 8, 8, 0) == fft3d.FFT3D_ERR_NULL
+
+
 def test_null_plan_calls(lib):
     assert lib.fft3d_plan_destroy(None) == fft3d.FFT3D_OK
     for f in ("fft3d_exec_r2c", "fft3d_exec_c2r", "fft3d_exec_r2c_adjoint", "fft3d_exec_c2r_adjoint"):
