@@ -346,27 +346,47 @@ def run_ours(args):
     host_in.copy_(buf32[..., :n])
     host_out = torch.empty_like(host_in, pin_memory=True)
     del buf32
-    dev_cplx = plan32.empty_complex()
-    stream = torch.cuda.current_stream(dev)
-    e2e_steps = max(2, args.steps // 10)
+    e2e_steps = 2 * max(1, args.steps // 20)
 
-    def e2e_step():
-        plan32.r2c(host_in, dev_cplx)
-        plan32.c2r_overwrite(dev_cplx, host_out)
+    def e2e_time(nstreams):
+        """ms per pair with `nstreams` fields in flight (one plan, spectrum
+        buffer and output per stream; pair k runs on stream k mod nstreams)."""
+        plans = [plan32] + [fft3d.Plan(grid, torch.float32, dev) for _ in range(nstreams - 1)]
+        cplx = [p.empty_complex() for p in plans]
+        outs = [host_out] + [torch.empty_like(host_in, pin_memory=True) for _ in range(nstreams - 1)]
+        main = torch.cuda.current_stream(dev)
+        streams = [main] + [torch.cuda.Stream(dev) for _ in range(nstreams - 1)]
 
-    for _ in range(2):
-        e2e_step()
-    torch.cuda.synchronize(dev)
-    if pg is not None:
-        pg.barrier()
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(e2e_steps):
-        e2e_step()
-    b.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_e2e = max_over_ranks(a.elapsed_time(b), pg, dev) / e2e_steps
+        def step(k):
+            i = k % nstreams
+            with torch.cuda.stream(streams[i]):
+                plans[i].r2c(host_in, cplx[i])
+                plans[i].c2r_overwrite(cplx[i], outs[i])
+
+        for k in range(2 * nstreams):
+            step(k)
+        torch.cuda.synchronize(dev)
+        if pg is not None:
+            pg.barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(main)
+        for st in streams[1:]:
+            st.wait_stream(main)
+        for k in range(e2e_steps):
+            step(k)
+        for st in streams[1:]:
+            main.wait_stream(st)
+        b.record(main)
+        torch.cuda.synchronize(dev)
+        ms = max_over_ranks(a.elapsed_time(b), pg, dev) / e2e_steps
+        del plans, cplx, outs[1:]
+        torch.cuda.empty_cache()
+        return ms
+
+    ms_e2e_1 = e2e_time(1)
+    ms_e2e_2 = e2e_time(2)
+    ms_e2e = min(ms_e2e_1, ms_e2e_2)
     e2e_val = flops * world / (ms_e2e * 1e-3) / 1e9
     io_bytes = n0 * n1 * n * 4
 
@@ -392,8 +412,11 @@ def run_ours(args):
                  "fp32_speedup": round(t64 / t_step, 2)},
         "e2e": {"value": round(e2e_val, 1), "unit": UNIT, "ms_per_step": round(ms_e2e, 3),
                 "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
+                "ms_per_step_one_stream": round(ms_e2e_1, 3), "ms_per_step_two_streams": round(ms_e2e_2, 3),
                 "how": "pinned host field read by the forward's first pass and written by the inverse's last "
-                       "pass over the CPU-GPU link (fft3d_exec_r2c / fft3d_exec_c2r_overwrite)"},
+                       "pass over the CPU-GPU link (fft3d_exec_r2c / fft3d_exec_c2r_overwrite); value = the "
+                       "faster of one stream and two streams with a field in flight on each (one plan, "
+                       "spectrum and output buffer per stream)"},
         "gpu_launches": int(launches32),
         "clocks": clk,
         "peak_source": peaks["src"],

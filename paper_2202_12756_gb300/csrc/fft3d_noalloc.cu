@@ -162,6 +162,7 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
         a.nyq_in_plane = 0;
         a.bulk = 0;
         a.err = err_flag;
+        a.early = 0;
         e = f32 ? col_launch_f32((int)n0, a, tiles, tw0, nullptr, nullptr, st) : col_launch_f64((int)n0, a, tiles, tw0, nullptr, nullptr, st);
         if (e != cudaSuccess) return FFT3D_ERR_CUDA;
     }
@@ -179,6 +180,7 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
         a.nyq_in_plane = 0;
         a.bulk = 0;
         a.err = err_flag;
+        a.early = 0;
         a.tiles_per_field = 1;
         const int64_t tiles = a.tiles_main + (n0 + g1.per_block - 1) / g1.per_block;
         e = f32 ? col_launch_f32((int)n1, a, tiles, tw1, nullptr, nullptr, st) : col_launch_f64((int)n1, a, tiles, tw1, nullptr, nullptr, st);
@@ -192,6 +194,7 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
     z.nlines = n0 * n1;
     z.scale_edge = 1.0;
     z.scale_mid = 1.0 / ((double)n0 * (double)n1 * (double)n2);
+    z.max_blocks = 0;
     e = f32 ? zc2r_launch_f32((int)m, z, twz, rot, st) : zc2r_launch_f64((int)m, z, twz, rot, st);
     return e == cudaSuccess ? FFT3D_OK : FFT3D_ERR_CUDA;
 }

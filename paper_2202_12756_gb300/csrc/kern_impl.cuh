@@ -95,11 +95,16 @@ template <typename R, int L> inline cudaError_t col_prepare_t()
     col_geom_t<R, L>(&g);
     cudaError_t e;
     if constexpr (col_pipe<R, L>()) {
-        e = cudaFuncSetAttribute(colpass_pipe_kernel<R, L, col_E<R, L>(), col_W<R, L>(), false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
-        if (e != cudaSuccess) return e;
-        return cudaFuncSetAttribute(colpass_pipe_kernel<R, L, col_E<R, L>(), col_W<R, L>(), true>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+        constexpr int E = col_E<R, L>(), W = col_W<R, L>();
+        const void *const ks[4] = {(const void *)colpass_pipe_kernel<R, L, E, W, false, false>,
+                                   (const void *)colpass_pipe_kernel<R, L, E, W, true, false>,
+                                   (const void *)colpass_pipe_kernel<R, L, E, W, false, true>,
+                                   (const void *)colpass_pipe_kernel<R, L, E, W, true, true>};
+        for (const void *k : ks) {
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
     } else {
         e = cudaFuncSetAttribute(colpass_kernel<R, L, col_E<R, L>(), col_W<R, L>(), false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
@@ -113,11 +118,16 @@ template <typename R, int M> inline cudaError_t z_prepare_t()
 {
     PassGeom g;
     z_geom_t<R, M>(&g);
-    cudaError_t e = cudaFuncSetAttribute(zpass_r2c_kernel<R, M, z_E<R, M>(), z_LPB<R, M>()>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(zpass_c2r_kernel<R, M, z_E<R, M>(), z_LPB<R, M>()>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+    constexpr int E = z_E<R, M>(), LPB = z_LPB<R, M>();
+    const void *const ks[4] = {(const void *)zpass_r2c_kernel<R, M, E, LPB, false>,
+                               (const void *)zpass_r2c_kernel<R, M, E, LPB, true>,
+                               (const void *)zpass_c2r_kernel<R, M, E, LPB, false>,
+                               (const void *)zpass_c2r_kernel<R, M, E, LPB, true>};
+    for (const void *k : ks) {
+        const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // Resident blocks of a persistent kernel on the current device, cached per
@@ -165,8 +175,11 @@ inline cudaError_t col_launch_t(const ColArgs &a, int64_t tiles, const void *tw,
     col_geom_t<R, L>(&g);
     typedef const typename cvec<R>::T *TW;
     if constexpr (col_pipe<R, L>()) {
-        auto k = a.inverse ? colpass_pipe_kernel<R, L, col_E<R, L>(), col_W<R, L>(), true>
-                           : colpass_pipe_kernel<R, L, col_E<R, L>(), col_W<R, L>(), false>;
+        constexpr int E = col_E<R, L>(), W = col_W<R, L>();
+        auto k = a.early ? (a.inverse ? colpass_pipe_kernel<R, L, E, W, true, true>
+                                      : colpass_pipe_kernel<R, L, E, W, false, true>)
+                         : (a.inverse ? colpass_pipe_kernel<R, L, E, W, true, false>
+                                      : colpass_pipe_kernel<R, L, E, W, false, false>);
         const int grid = persistent_grid(k, g.threads, g.smem, tiles);
         CUtensorMap map, map2;
         if (tmap) map = *tmap;
@@ -187,9 +200,13 @@ inline cudaError_t zr2c_launch_t(const ZArgs &a, const void *tw, const void *rot
 {
     PassGeom g;
     z_geom_t<R, M>(&g);
+    constexpr int E = z_E<R, M>(), LPB = z_LPB<R, M>();
     const int64_t blocks = (a.nlines + g.per_block - 1) / g.per_block;
-    zpass_r2c_kernel<R, M, z_E<R, M>(), z_LPB<R, M>()><<<(unsigned)blocks, g.threads, g.smem, st>>>(
-        a, (const typename cvec<R>::T *)tw, (const typename cvec<R>::T *)rot);
+    typedef const typename cvec<R>::T *TW;
+    if (a.max_blocks > 0 && blocks > a.max_blocks)
+        zpass_r2c_kernel<R, M, E, LPB, true><<<(unsigned)a.max_blocks, g.threads, g.smem, st>>>(a, (TW)tw, (TW)rot);
+    else
+        zpass_r2c_kernel<R, M, E, LPB, false><<<(unsigned)blocks, g.threads, g.smem, st>>>(a, (TW)tw, (TW)rot);
     return cudaGetLastError();
 }
 
@@ -198,9 +215,13 @@ inline cudaError_t zc2r_launch_t(const ZArgs &a, const void *tw, const void *rot
 {
     PassGeom g;
     z_geom_t<R, M>(&g);
+    constexpr int E = z_E<R, M>(), LPB = z_LPB<R, M>();
     const int64_t blocks = (a.nlines + g.per_block - 1) / g.per_block;
-    zpass_c2r_kernel<R, M, z_E<R, M>(), z_LPB<R, M>()><<<(unsigned)blocks, g.threads, g.smem, st>>>(
-        a, (const typename cvec<R>::T *)tw, (const typename cvec<R>::T *)rot);
+    typedef const typename cvec<R>::T *TW;
+    if (a.max_blocks > 0 && blocks > a.max_blocks)
+        zpass_c2r_kernel<R, M, E, LPB, true><<<(unsigned)a.max_blocks, g.threads, g.smem, st>>>(a, (TW)tw, (TW)rot);
+    else
+        zpass_c2r_kernel<R, M, E, LPB, false><<<(unsigned)blocks, g.threads, g.smem, st>>>(a, (TW)tw, (TW)rot);
     return cudaGetLastError();
 }
 

@@ -52,6 +52,8 @@ struct ColArgs {
                               // 2 TMA (y-pass rows of odd complex pitch, even / odd row maps)
     unsigned *err;            // pipelined pass: device error flag (a stage-fill wait ran out)
     int64_t tiles_per_field;  // x-pass: tiles of one field; field b's columns start at row k0 = b n0
+    int early;                // pipelined pass: stage the next tile before the current one's first stage
+                              // (selects the kernel instance)
 };
 
 template <typename C>
@@ -251,12 +253,6 @@ constexpr int kTmaBoxRows = 256;
 template <typename C, int W> __host__ __device__ constexpr int stage_row_elems() { return W; }
 template <typename C, int W, int L> __host__ __device__ constexpr int stage_elems() { return L / 2 * W + L / 2 * (W + 2); }
 
-// Stage the next tile as soon as the current one is in registers (one extra
-// barrier per tile), instead of after the first exchange barrier.
-#ifndef FFT3D_PIPE_EARLY_PREFETCH
-#define FFT3D_PIPE_EARLY_PREFETCH 0
-#endif
-
 // polls of a stage-fill wait before the kernel gives up (about 0.1 s)
 constexpr long long kStageWaitPolls = 1LL << 22;
 
@@ -291,11 +287,15 @@ template <typename R, int L, int E, int W> __host__ __device__ constexpr size_t 
 // shared memory once per block (a thread's twiddles are the same in every
 // tile).  The tile is W = 16 float2 columns: 128-byte row segments, which
 // HBM serves at about twice the rate of 64-byte ones at this row stride.
+// With EARLY the next tile is staged as soon as the current one is in
+// registers (one barrier more per tile) rather than after the first exchange
+// barrier; which is faster depends on the access pattern (ColArgs::early,
+// set by the host, selects the instance).
 // Measured on GB300, two alternatives were slower: exchanging through the
 // staging buffer itself (so the next tile's copies start only after the
 // exchange) by 35-40%, and waiting for the next tile before storing this one
 // (stores interleaved with the next tile's staging reads) by 9-25%.
-template <typename R, int L, int E, int W, bool INV>
+template <typename R, int L, int E, int W, bool INV, bool EARLY>
 __global__ void __launch_bounds__(W *(L / E), (W * (L / E) >= 512 ? 1 : 512 / (W * (L / E))))
 colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64_t ntiles,
                     const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap2)
@@ -419,14 +419,14 @@ colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
         auto next = [&]() {
             if (tn < ntiles) moden = fill(tn, spn, ssn);
         };
-#if FFT3D_PIPE_EARLY_PREFETCH
-        // every thread has its elements of tile t in registers: stage tile tn now
-        __syncthreads();
-        next();
-        line_fft<R, L, E, true>(v, j, tws, ex);
-#else
-        line_fft<R, L, E, true>(v, j, tws, ex, next);
-#endif
+        if constexpr (EARLY) {
+            // every thread has its elements of tile t in registers: stage tile tn now
+            __syncthreads();
+            next();
+            line_fft<R, L, E, true>(v, j, tws, ex);
+        } else {
+            line_fft<R, L, E, true>(v, j, tws, ex, next);
+        }
         if (valid) {
             C *dj = dp + (int64_t)j * ds;
             const int64_t dstep = (int64_t)NT * ds;
@@ -457,6 +457,7 @@ struct ZArgs {
     int64_t nlines;       // N0 * N1
     double scale_edge;    // r2c: factor on k2 = 0 and M outputs; c2r: weight of k2 = 0, M inputs
     double scale_mid;     // r2c: factor on the other outputs;    c2r: output factor
+    int64_t max_blocks;   // > 0: launch at most this many blocks, each looping over line groups
 };
 
 // Elements per thread of a z-pass line: the default plan of the length (16,
@@ -669,22 +670,40 @@ __device__ __forceinline__ void zc2r_lines(const ZArgs &a, int64_t line0, unsign
     }
 }
 
-template <typename R, int M, int E, int LPB>
+// One group of LPB lines per block; with LOOP, a grid of a.max_blocks blocks
+// walks the line groups (the host-memory form, bound by the CPU-GPU link).
+// Two instances because the loop slows the one-pass form down (up to 20%
+// measured for the C2R lines on GB300).
+template <typename R, int M, int E, int LPB, bool LOOP>
 __global__ void __launch_bounds__(LPB *(M / E))
 zpass_r2c_kernel(ZArgs a, const typename cvec<R>::T *__restrict__ tw,
                  const typename cvec<R>::T *__restrict__ rot)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    zr2c_lines<R, M, E, LPB>(a, (int64_t)blockIdx.x * LPB, smem_raw, tw, rot);
+    if constexpr (LOOP) {
+        for (int64_t blk = blockIdx.x; blk * LPB < a.nlines; blk += gridDim.x) {
+            if (blk != blockIdx.x) __syncthreads();  // shared memory free for the next line group
+            zr2c_lines<R, M, E, LPB>(a, blk * LPB, smem_raw, tw, rot);
+        }
+    } else {
+        zr2c_lines<R, M, E, LPB>(a, (int64_t)blockIdx.x * LPB, smem_raw, tw, rot);
+    }
 }
 
-template <typename R, int M, int E, int LPB>
+template <typename R, int M, int E, int LPB, bool LOOP>
 __global__ void __launch_bounds__(LPB *(M / E))
 zpass_c2r_kernel(ZArgs a, const typename cvec<R>::T *__restrict__ tw,
                  const typename cvec<R>::T *__restrict__ rot)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    zc2r_lines<R, M, E, LPB, false>(a, (int64_t)blockIdx.x * LPB, smem_raw, tw, rot);
+    if constexpr (LOOP) {
+        for (int64_t blk = blockIdx.x; blk * LPB < a.nlines; blk += gridDim.x) {
+            if (blk != blockIdx.x) __syncthreads();  // shared memory free for the next line group
+            zc2r_lines<R, M, E, LPB, false>(a, blk * LPB, smem_raw, tw, rot);
+        }
+    } else {
+        zc2r_lines<R, M, E, LPB, false>(a, (int64_t)blockIdx.x * LPB, smem_raw, tw, rot);
+    }
 }
 
 // ------------------------------------------------------------ twiddles
