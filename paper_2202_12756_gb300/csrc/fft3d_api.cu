@@ -350,7 +350,7 @@ int check_exec(fft3d_plan p, const void *in, const void *out, bool real_in)
 // (grid-stride over line groups) and leaves the others to the strided passes
 // of another stream (another field in flight).
 #ifndef FFT3D_HOST_Z_BLOCKS
-#define FFT3D_HOST_Z_BLOCKS 192
+#define FFT3D_HOST_Z_BLOCKS 384
 #endif
 
 // True for memory the GPU reaches over the CPU-GPU link (pinned, registered
