@@ -197,21 +197,24 @@ int fft3d_plan_launch_count(fft3d_plan plan, int64_t *count);
 int fft3d_plan_set_fused(fft3d_plan plan, int enable);
 
 /*
- * Device-side error flag of the plan's fused plane pass (see
- * fft3d_plan_set_fused), whose blocks wait on per-plane counters.
- * Each such wait is bounded; a wait that runs out makes every block of that
- * launch stop early (the output is then invalid) and sets this flag.
- * fft3d_plan_status synchronises the device, stores the flag (0 or 1) in
- * *device_error and clears it.  Plans without the fused pass always report 0.
+ * Device-side error flag of the plan's kernels that wait: the fused plane
+ * pass (see fft3d_plan_set_fused), whose blocks wait on per-plane counters,
+ * and the pipelined FP32 column passes, whose blocks wait on an mbarrier for
+ * the TMA copies of their next tile.  Each such wait is bounded; a wait that
+ * runs out makes the waiting blocks stop early (the output is then invalid)
+ * and sets this flag.  fft3d_plan_status synchronises the device, stores the
+ * flag (0 or 1) in *device_error and clears it.
  */
 int fft3d_plan_status(fft3d_plan plan, int *device_error);
 
 /*
  * Test hook for the bounded waits above: with inject_stall != 0 every
- * waiting block waits for one producer more than exists, so its wait runs
- * out after `spin_limit` polls (about 0.1 us each; <= 0 restores the default
- * of about one second) and fft3d_plan_status then reports the error.  Keep
- * inject_stall = 0 outside such tests.
+ * waiting block of the fused pass waits for one producer more than exists,
+ * and every tile wait of a pipelined column pass expects 16 bytes more than
+ * its copies deliver, so the waits run out after `spin_limit` polls (about
+ * 0.1 us each; <= 0 restores the defaults of about one second for the fused
+ * pass and 0.1 s per tile wait) and fft3d_plan_status then reports the
+ * error.  Keep inject_stall = 0 outside such tests.
  */
 int fft3d_plan_set_debug(fft3d_plan plan, int inject_stall, int64_t spin_limit);
 

@@ -179,20 +179,28 @@ bool tensor_map_2d(const void *base, int64_t inner, int64_t rows, int64_t pitch,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Tile waits of a pipelined column pass: normal, or made to run out (test hook).
+void set_stage_waits(const fft3d_plan_s *p, ColArgs &a)
+{
+    a.stall_tx = p->inject_stall ? 16u : 0u;
+    a.stage_polls = p->inject_stall ? p->spin_limit : kStageWaitPolls;
+}
+
 // TMA mode of a pipelined column pass over `src` (see colpass_pipe_kernel):
 // 0 = per-element copies; 1 = one map over 16-byte aligned rows; 2 = even /
 // odd row maps (y-pass rows of odd complex pitch).  Needs float, the
-// pipelined kernel for this length, a standard layout at a 16-byte aligned
-// base, full tiles, and L a multiple of 512.
+// pipelined kernel for this length, a 16-byte aligned base, full tiles, and
+// L a multiple of 512; the split layout (rows of pitch M plus the k2 = M
+// plane) takes mode 1 in the y-pass (its k2 = M tiles use per-element copies).
 int bulk_mode(const fft3d_plan_s *p, const CLayout &src, int axis, int64_t w)
 {
     const PassGeom &g = axis == 0 ? p->g0 : p->g1;
     const int64_t L = axis == 0 ? p->n0 : p->n1;
-    if (!g.persistent || p->dtype != FFT3D_F32 || src.split || ((uintptr_t)src.main & 15) ||
-        L % (2 * kTmaBoxRows) != 0)
+    if (!g.persistent || p->dtype != FFT3D_F32 || ((uintptr_t)src.main & 15) || L % (2 * kTmaBoxRows) != 0)
         return 0;
-    if (axis == 0) return ((p->n1 * p->m1) % 2 == 0 && (p->n1 * p->m1) % w == 0) ? 1 : 0;
+    if (axis == 0) return (!src.split && (p->n1 * p->m1) % 2 == 0 && (p->n1 * p->m1) % w == 0) ? 1 : 0;
     if (p->m % w != 0) return 0;
+    if (src.split) return 1;  // main rows of pitch M (a multiple of W): 16-byte aligned
     return (p->m1 % 2 == 0) ? 1 : 2;
 }
 
@@ -217,6 +225,7 @@ ColArgs ypass_args(const fft3d_plan_s *p, CLayout src, CLayout dst, int inverse,
     a.tiles_per_field = 1;
     // early staging measured faster for 1024-point y columns (-1..-15%), slower for 2048 (+1..2%)
     a.early = p->n1 == 1024;
+    set_stage_waits(p, a);
     *tiles = a.tiles_main + (p->nb0 + w - 1) / w;
     return a;
 }
@@ -244,6 +253,7 @@ ColArgs xpass_args(const fft3d_plan_s *p, CLayout src, CLayout dst, int inverse,
     a.nyq_in_plane = 0;
     a.bulk = bulk_mode(p, src, 0, w);
     a.err = p->status;
+    set_stage_waits(p, a);
     return a;
 }
 
@@ -270,6 +280,8 @@ int run_fused(fft3d_plan p, int kind, const ZArgs &z, CLayout ylayout, int forwa
     f.y.err = p->status;
     f.y.tiles_per_field = 1;
     f.y.early = 0;
+    f.y.stall_tx = 0;
+    f.y.stage_polls = kStageWaitPolls;
     f.n0 = p->n0;
     f.zi = p->n1 / p->fz_lines;
 #ifndef FFT3D_FUSED_LAG
@@ -297,7 +309,8 @@ int run_colpass(fft3d_plan p, int kind, ColArgs a, int64_t tiles, int L, const v
     if (a.bulk == 1 && a.axis == 0) {
         ok = tensor_map_2d(a.src.main, p->n1 * p->m1, p->nb0, p->n1 * p->m1, w, &map);
     } else if (a.bulk == 1) {
-        ok = tensor_map_2d(a.src.main, p->m1, p->nb0 * p->n1, p->m1, w, &map);
+        const int64_t pitch = a.src.split ? p->m : p->m1;  // the split layout's k2 < M rows
+        ok = tensor_map_2d(a.src.main, pitch, p->nb0 * p->n1, pitch, w, &map);
     } else if (a.bulk == 2) {
         ok = tensor_map_2d(a.src.main, 2 * p->m1, p->nb0 * p->n1 / 2, 2 * p->m1, w, &map) &&
              tensor_map_2d(a.src.main, 2 * p->m1, p->nb0 * p->n1 / 2, 2 * p->m1, w + 2, &map2);

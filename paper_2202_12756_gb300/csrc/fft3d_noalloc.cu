@@ -163,6 +163,8 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
         a.bulk = 0;
         a.err = err_flag;
         a.early = 0;
+        a.stall_tx = 0;
+        a.stage_polls = kStageWaitPolls;
         e = f32 ? col_launch_f32((int)n0, a, tiles, tw0, nullptr, nullptr, st) : col_launch_f64((int)n0, a, tiles, tw0, nullptr, nullptr, st);
         if (e != cudaSuccess) return FFT3D_ERR_CUDA;
     }
@@ -181,6 +183,8 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
         a.bulk = 0;
         a.err = err_flag;
         a.early = 0;
+        a.stall_tx = 0;
+        a.stage_polls = kStageWaitPolls;
         a.tiles_per_field = 1;
         const int64_t tiles = a.tiles_main + (n0 + g1.per_block - 1) / g1.per_block;
         e = f32 ? col_launch_f32((int)n1, a, tiles, tw1, nullptr, nullptr, st) : col_launch_f64((int)n1, a, tiles, tw1, nullptr, nullptr, st);

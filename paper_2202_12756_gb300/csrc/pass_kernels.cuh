@@ -54,6 +54,8 @@ struct ColArgs {
     int64_t tiles_per_field;  // x-pass: tiles of one field; field b's columns start at row k0 = b n0
     int early;                // pipelined pass: stage the next tile before the current one's first stage
                               // (selects the kernel instance)
+    unsigned stall_tx;        // pipelined pass, test hook: bytes a tile wait expects beyond its copies
+    long long stage_polls;    // pipelined pass: polls of a tile wait before it gives up
 };
 
 template <typename C>
@@ -331,7 +333,7 @@ colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
                 // order the block's earlier reads of the buffer before the async-proxy writes
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 if (mode == 1) {
-                    mbar_arrive_expect_tx(mb, (unsigned)(L * W * sizeof(C)));
+                    mbar_arrive_expect_tx(mb, (unsigned)(L * W * sizeof(C)) + a.stall_tx);
                     int x, y0;
                     if (a.axis == 0) {  // [B N0][N1 (M+1)]: the tile's flat columns, its field's rows
                         const int64_t b = (uint32_t)tt / (uint32_t)a.tiles_per_field;
@@ -346,7 +348,7 @@ colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
                     for (int b = 0; b < L / kTmaBoxRows; ++b)
                         tma_load_2d(smem_u32(stage + b * kTmaBoxRows * W), &tmap, x, y0 + b * kTmaBoxRows, mb);
                 } else {
-                    mbar_arrive_expect_tx(mb, (unsigned)(L / 2 * (2 * W + 2) * sizeof(C)));
+                    mbar_arrive_expect_tx(mb, (unsigned)(L / 2 * (2 * W + 2) * sizeof(C)) + a.stall_tx);
                     const int64_t k0 = tt / a.tiles_per_plane;
                     const int c0 = (int)((tt - k0 * a.tiles_per_plane) * W);
                     const int y0 = (int)(k0 * (a.n1 / 2));
@@ -388,10 +390,10 @@ colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
         const bool validn = tn < ntiles && col_decode<C, W>(a, tn, c, spn, ssn, dpn, dsn);
 
         if (mode) {
-            const bool ok = mbar_wait_bounded(mb, phase, kStageWaitPolls);
+            const bool ok = mbar_wait_bounded(mb, phase, a.stage_polls);
             if (__syncthreads_or(!ok)) {
                 if (threadIdx.x == 0) atomicOr(a.err, 1u);
-                mbar_wait_bounded(mb, phase, kStageWaitPolls);  // copies still in flight
+                mbar_wait_bounded(mb, phase, a.stage_polls);  // copies still in flight
                 return;
             }
             phase ^= 1u;

@@ -1,10 +1,12 @@
-"""Failure detection of the fused plane pass, without a GPU fault.
+"""Failure detection of the kernels that wait, without a GPU fault.
 
-The fused kernel's blocks wait on per-plane counters that other blocks set.
-Each wait is bounded.  Here the test hook makes every waiting block wait for
-one producer more than exists, with a short bound: the waits run out, the
-kernel returns early and raises its error flag, the host reads the flag, and
-the same plan then computes correctly again (the context stays usable)."""
+The fused kernel's blocks wait on per-plane counters that other blocks set,
+and the pipelined column kernel's blocks wait on an mbarrier for the TMA
+copies of their next tile.  Each wait is bounded.  Here the test hook makes
+the waits unsatisfiable (one producer more than exists; 16 bytes more than
+the copies deliver) with a short bound: the waits run out, the kernel returns
+early and raises its error flag, the host reads the flag, and the same plan
+then computes correctly again (the context stays usable)."""
 import numpy as np
 import pytest
 
@@ -55,3 +57,35 @@ def test_plans_without_fused_pass_report_no_error():
     assert not plan.info()["fused_plane_pass"]
     plan.r2c(torch.zeros((8, 16, 32), dtype=torch.float64, device="cuda"))
     assert plan.status() == 0
+
+
+@pytest.mark.parametrize("shape", [(1024, 16, 32), (8, 1024, 64)], ids=lambda s: "x".join(map(str, s)))
+def test_pipelined_tile_wait_reports_and_recovers(shape):
+    """The pipelined column kernel waits on an mbarrier for the TMA copies of
+    each tile.  With the test hook every tile wait expects 16 bytes more than
+    its copies deliver, so it runs out after a short bound: the blocks stop,
+    the flag is reported once, and the same plan then computes correctly.
+    (1024, 16, 32): x-pass over whole rows; (8, 1024, 64): y-pass with the
+    even/odd row-pair copies of an odd row pitch.)"""
+    import torch
+    import paper_2202_12756_gb300 as fft3d
+    plan = fft3d.Plan(shape, torch.float32)
+    f = synth.uniform_field(shape, 43).astype(np.float32)
+    x = torch.from_numpy(f).cuda()
+    X = plan.r2c(x)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+
+    plan.set_debug(True, spin_limit=1 << 14)
+    plan.r2c(x, X)
+    torch.cuda.synchronize()
+    assert plan.status() == 1, "the stalled tile wait was not reported"
+    assert plan.status() == 0, "the flag is cleared once read"
+
+    plan.set_debug(False)
+    X2 = plan.r2c(x)
+    back = plan.c2r(X2)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    assert rel_l2(X2.cpu().numpy(), oracle.rfft3(f.astype(np.float64))) <= TOL["f32"]
+    assert rel_l2(back.cpu().numpy(), f) <= TOL["f32"]
