@@ -186,21 +186,21 @@ def time_pairs(plan, buf, steps, warmup, dev, pg, profile=False):
     plan.profile_read()  # clear
     plan.set_profiling(profile)
     l0 = plan.launch_count()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    for k in range(steps):
         plan.r2c_(buf)
         plan.c2r_(buf)
-    e1.record(stream)
+        ev[k + 1].record(stream)
     torch.cuda.synchronize(dev)
     if pg is not None:
         pg.barrier()
-    ms = e0.elapsed_time(e1)
+    ms = ev[0].elapsed_time(ev[-1])
+    per_step = sorted(ev[k].elapsed_time(ev[k + 1]) for k in range(steps))
     launches = plan.launch_count() - l0
     stats = plan.profile_read() if profile else []
     plan.set_profiling(False)
-    return ms, launches, stats
+    return ms, launches, stats, per_step
 
 
 def roofline_from(stats, peak_gbs, traffic):
@@ -320,7 +320,7 @@ def run_ours(args):
     # ---- FP32 headline: device-resident inputs
     clocks = ClockSampler(local)
     clocks.start()
-    ms32, launches32, stats32 = time_pairs(plan32, buf32, args.steps, args.warmup, dev, pg, profile=True)
+    ms32, launches32, stats32, steps32 = time_pairs(plan32, buf32, args.steps, args.warmup, dev, pg, profile=True)
     clk = clocks.stop()
     ms32 = max_over_ranks(ms32, pg, dev)
     t_step = ms32 / args.steps
@@ -333,7 +333,7 @@ def run_ours(args):
 
     # ---- FP64 pair (same field)
     steps64 = max(2, args.steps // 10)
-    ms64, launches64, stats64 = time_pairs(plan64, buf64, steps64, args.warmup, dev, pg, profile=True)
+    ms64, launches64, stats64, _ = time_pairs(plan64, buf64, steps64, args.warmup, dev, pg, profile=True)
     ms64 = max_over_ranks(ms64, pg, dev)
     t64 = ms64 / steps64
     del buf64
@@ -395,6 +395,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_step, 4),
+        "ms_per_step_min": round(steps32[0], 4), "ms_per_step_median": round(steps32[len(steps32) // 2], 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": f"{gname} real grid, R2C+C2R pair in place (padded rows), FP32, "
