@@ -270,6 +270,19 @@ def round_trip_error(plan, host_in, host_out):
     return float(d)
 
 
+def workload_config(grid, world):
+    """The `config` of the bench line (both arms)."""
+    n0, n1, n = grid
+    return {"workload": f"{n0}x{n1}x{n} real grid, R2C+C2R pair in place (padded rows), FP32, "
+                        f"turbulence-like field (|k|^-11/6, seed 2)",
+            "grid": list(grid), "layout": "in-place padded", "parallelism": f"replicas x{world}",
+            "l2": f"inputs ({n0 * n1 * (n // 2 + 1) * 8 / 1e9:.2f} GB) larger than L2, no flush"}
+
+
+def bench_grid(args):
+    return tuple(int(x) for x in args.grid.split(",")) if args.grid else (args.n,) * 3
+
+
 def run_reference(args):
     world, rank, local, pg = dist_setup(args)
     if rank != 0:
@@ -289,10 +302,11 @@ def run_reference(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.n}^3 R2C+C2R pair; reference arm: FP64 CPU oracle on a "
-                                   f"{n}^3 sample per step", "grid": [n, n, n]},
+            "config": workload_config(bench_grid(args), world),
             "cpu_baseline": {"value": round(val, 3), "unit": UNIT, "cores": oracle.num_threads(),
-                             "kind": "oracle", "sample": f"one {n}^3 FP64 pair per step"},
+                             "kind": "oracle",
+                             "sample": f"each step one FP64 R2C+C2R pair of a {n}^3 uniform field (the oracle "
+                                       f"as it stands; the GFLOP/s rate uses that pair's flops)"},
             "e2e": {"value": round(val, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -305,7 +319,7 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     import paper_2202_12756_gb300 as fft3d
     fft3d.load_library()
-    grid = tuple(int(x) for x in args.grid.split(",")) if args.grid else (args.n,) * 3
+    grid = bench_grid(args)
     n0, n1, n = grid
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"]
@@ -398,10 +412,7 @@ def run_ours(args):
         "ms_per_step_min": round(steps32[0], 4), "ms_per_step_median": round(steps32[len(steps32) // 2], 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"{gname} real grid, R2C+C2R pair in place (padded rows), FP32, "
-                               f"turbulence-like field (|k|^-11/6, seed 2)",
-                   "grid": list(grid), "layout": "in-place padded", "parallelism": f"replicas x{world}",
-                   "l2": f"inputs ({n0 * n1 * (n // 2 + 1) * 8 / 1e9:.2f} GB) larger than L2, no flush"},
+        "config": workload_config(grid, world),
         "hbm_gbs": round(bytes_pair / (t_step * 1e-3) / 1e9, 1),
         "hbm_frac_of_peak": round(bytes_pair / (t_step * 1e-3) / 1e9 / peak, 4),
         "gflops_paper_convention": round(2 * value, 1),
