@@ -42,7 +42,7 @@ struct CLayout {
 
 struct ColArgs {
     CLayout src, dst;
-    int64_t n0, n1, m;        // grid N0, N1 and M = N2 / 2
+    int64_t n0, n1, m;        // N0 (x-pass: column length; y-pass: planes of all fields, B N0), N1, M = N2 / 2
     int axis;                 // 0: rows are k0 (x-pass); 1: rows are k1 (y-pass)
     int inverse;              // 1: exp(+...) via swapped re / im in and out
     int64_t tiles_main;       // tiles of the main column set
