@@ -142,6 +142,19 @@ template <typename R, int W> struct ColSplitEx {
     __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 
+// Stores of pass outputs: the next pass reads them back from HBM (an array
+// far larger than L2), so they are marked evict-first (st.global.cs).
+// Measured on GB300 at 1024^3 FP32: the R2C z-pass 3.4% and the whole pair
+// 0.8% faster; at 1536^3 the pair is 0.5% slower.
+#ifndef FFT3D_STORE_CS
+#define FFT3D_STORE_CS 1
+#endif
+template <typename C> __device__ __forceinline__ void store_out(C *p, C v)
+{
+    if constexpr (FFT3D_STORE_CS) __stcs(p, v);
+    else *p = v;
+}
+
 // Loads that bypass L1: a tile written earlier in the same kernel by another
 // block is read from L2, never from a stale L1 line.
 template <typename C> __device__ __forceinline__ C load_cg(const C *p) { return __ldcg(p); }
@@ -436,7 +449,7 @@ colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
             for (int i = 0; i < E; ++i) {
                 C o = v[i];
                 if (INV) o = cswap(o);
-                dj[i * dstep] = o;
+                store_out(dj + i * dstep, o);
             }
         }
         t = tn;
@@ -548,7 +561,7 @@ __device__ __forceinline__ void zr2c_lines(const ZArgs &a, int64_t line0, unsign
         const C s = cadd(z, zc);          // 2 E[k]
         const C d = cmul(r, csub(z, zc));  // 2i W^k O[k]
         const R f = R(0.5) * (k == 0 ? se : sm);
-        if (active) out[k] = cmake<C>(f * (s.x + d.y), f * (s.y - d.x));
+        if (active) store_out(out + k, cmake<C>(f * (s.x + d.y), f * (s.y - d.x)));
     };
     if constexpr (NT <= 32 && sizeof(R) == 4) {
         const int src = (NT - j) & (NT - 1);
@@ -668,7 +681,7 @@ __device__ __forceinline__ void zc2r_lines(const ZArgs &a, int64_t line0, unsign
     C *out = (C *)((R *)a.real_out + l * a.real_pitch);
     if (active) {
 #pragma unroll
-        for (int i = 0; i < E; ++i) out[j + i * NT] = cmake<C>(s * v[i].x, -s * v[i].y);
+        for (int i = 0; i < E; ++i) store_out(out + j + i * NT, cmake<C>(s * v[i].x, -s * v[i].y));
     }
 }
 
