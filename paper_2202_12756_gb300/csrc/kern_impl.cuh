@@ -86,7 +86,7 @@ template <typename R, int M> inline void z_geom_t(PassGeom *g)
     g->per_block = LPB;
     g->E = z_E<R, M>();
     g->persistent = 0;
-    g->smem = (size_t)LPB * zline_smem_elems<M>() * sizeof(typename cvec<R>::T);
+    g->smem = (size_t)LPB * zline_smem_elems<M, z_E<R, M>()>() * sizeof(typename cvec<R>::T);
 }
 
 template <typename R, int L> inline cudaError_t col_prepare_t()
@@ -240,7 +240,7 @@ template <typename R, int N1, int M> inline void fused_geom_t(PassGeom *g, int *
     typedef FusedShape<N1, M> S;
     const size_t cs = sizeof(typename cvec<R>::T);
     const size_t y = (size_t)N1 * S::W * cs;
-    const size_t z = (size_t)S::LPB * zline_smem_elems<M>() * cs;
+    const size_t z = (size_t)S::LPB * zline_smem_elems<M, z_E<float, M>()>() * cs;
     g->threads = S::T;
     g->per_block = S::W;
     g->E = line_E(N1);

@@ -217,6 +217,67 @@ template <typename C> struct Dft<32, C> {
     }
 };
 
+// z * exp(-2 pi i p / 24) for a compile-time p; the multiples of 3 are
+// cheaper (W8 rotations, -i, -1).
+template <int P, typename C> __device__ __forceinline__ C w24(C z)
+{
+    constexpr int p = P % 24;
+    if constexpr (p == 0) {
+        return z;
+    } else if constexpr (p == 3) {
+        return w8_1(z);
+    } else if constexpr (p == 6) {
+        return cmul_mi(z);
+    } else if constexpr (p == 9) {
+        return w8_3(z);
+    } else if constexpr (p == 12) {
+        return cmake<C>(-z.x, -z.y);
+    } else {
+        constexpr CtCosSin w = ct_cossin_pi(-2LL * p, 24);
+        return cmulk(z, w.c, w.s);
+    }
+}
+
+template <typename C> struct Dft<24, C> {
+    // radix 8 x 3: n = 3 n1 + n2, k = k1 + 8 k2;
+    // y[k1 + 8 k2] = sum_{n2} W3^{n2 k2} W24^{n2 k1} sum_{n1} a[3 n1 + n2] W8^{n1 k1}
+    __device__ __forceinline__ static void run(C *a)
+    {
+        C b0[8], b1[8], b2[8];
+#pragma unroll
+        for (int n1 = 0; n1 < 8; ++n1) {
+            b0[n1] = a[3 * n1];
+            b1[n1] = a[3 * n1 + 1];
+            b2[n1] = a[3 * n1 + 2];
+        }
+        Dft<8, C>::run(b0);
+        Dft<8, C>::run(b1);
+        Dft<8, C>::run(b2);
+        b1[1] = w24<1>(b1[1]);
+        b1[2] = w24<2>(b1[2]);
+        b1[3] = w24<3>(b1[3]);
+        b1[4] = w24<4>(b1[4]);
+        b1[5] = w24<5>(b1[5]);
+        b1[6] = w24<6>(b1[6]);
+        b1[7] = w24<7>(b1[7]);
+        b2[1] = w24<2>(b2[1]);
+        b2[2] = w24<4>(b2[2]);
+        b2[3] = w24<6>(b2[3]);
+        b2[4] = w24<8>(b2[4]);
+        b2[5] = w24<10>(b2[5]);
+        b2[6] = w24<12>(b2[6]);
+        b2[7] = w24<14>(b2[7]);
+#pragma unroll
+        for (int k1 = 0; k1 < 8; ++k1) {
+            C t[3] = {b0[k1], b1[k1], b2[k1]};
+            Dft<3, C>::run(t);
+            a[k1] = t[0];
+            a[k1 + 8] = t[1];
+            a[k1 + 16] = t[2];
+        }
+    }
+};
+
 // Stockham stage s of a length-L line, E elements per thread.  Thread j holds
 // v[i] = x[j + i NT].  Butterfly b = j + q NT (q < E / R) combines
 // x[b + m L/R], m < R, which are v[q + m E/R]; with k = b mod Ns it applies

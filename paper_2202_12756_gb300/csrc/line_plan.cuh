@@ -7,8 +7,8 @@
 // Stockham autosort FFT: stage s combines R_s sub-transforms of length
 // Ns = R_0 * .. * R_{s-1}, so the output comes out in natural order with no
 // bit reversal.  Power-of-two lengths use radix min(E, 32) (then one smaller
-// radix); 3 * 2^k lengths use one radix-3 stage followed by radix 8 (then
-// smaller).
+// radix); 3 * 2^k lengths start with one radix-24 (3 x 8) or radix-3 stage,
+// followed by radix 8 (then smaller).
 #pragma once
 
 #include <stdint.h>
@@ -30,6 +30,16 @@ __host__ __device__ constexpr int line_E(int L)
 
 __host__ __device__ constexpr int line_NT(int L) { return L / line_E(L); }
 
+// First stage of a 3 * 2^k length: radix 24 (a 3 x 8 butterfly, one stage and
+// one exchange fewer) when E and L allow it, else radix 3.
+#ifndef FFT3D_RADIX24
+#define FFT3D_RADIX24 1
+#endif
+__host__ __device__ constexpr int line_first3(int L, int E)
+{
+    return (FFT3D_RADIX24 && E % 24 == 0 && (L / 3) % 8 == 0) ? 24 : 3;
+}
+
 // largest power-of-two radix used with E elements per thread
 __host__ __device__ constexpr int line_cap(int L, int E)
 {
@@ -40,7 +50,7 @@ __host__ __device__ constexpr int line_nstages(int L, int E)
 {
     int rem = L, s = 0;
     if (!is_pow2(L)) {
-        rem /= 3;
+        rem /= line_first3(L, E);
         s = 1;
     }
     const int cap = line_cap(L, E);
@@ -56,8 +66,8 @@ __host__ __device__ constexpr int line_radix(int L, int E, int s)
 {
     int rem = L, i = 0;
     if (!is_pow2(L)) {
-        if (s == 0) return 3;
-        rem /= 3;
+        if (s == 0) return line_first3(L, E);
+        rem /= line_first3(L, E);
         i = 1;
     }
     const int cap = line_cap(L, E);

@@ -481,12 +481,13 @@ struct ZArgs {
 // at M = 512, halves the resident warps and runs 25% slower.
 template <typename R, int M> __host__ __device__ constexpr int z_E() { return line_E(M); }
 
-// Per-line shared-memory exchange with one padding slot every 16 elements,
-// which makes the stride-16 writes of a radix-16 first stage conflict-free.
-// Indices arrive padded (i + (i >> 4), see pad_row).
-template <typename C, int NT> struct LineEx {
+// Per-line shared-memory exchange with one padding slot every 2^P elements:
+// P = 4 makes the stride-16 writes of a radix-16 first stage conflict-free,
+// P = 3 the stride-24 writes of a radix-24 one.  Indices arrive padded
+// (i + (i >> P), see pad_row).
+template <typename C, int NT, int P> struct LineEx {
     static constexpr bool kSplit = false;
-    static constexpr int kPadShift = 4;
+    static constexpr int kPadShift = P;
     C *sm;
     __device__ __forceinline__ void put(int pi, C v) { sm[pi] = v; }
     __device__ __forceinline__ C get(int pi) const { return sm[pi]; }
@@ -497,7 +498,11 @@ template <typename C, int NT> struct LineEx {
     }
 };
 
-template <int M> __host__ __device__ constexpr int zline_smem_elems() { return (M + 1) + ((M + 1) >> 4) + 1; }
+template <int E> __host__ __device__ constexpr int zline_pad() { return E % 3 == 0 ? 3 : 4; }
+template <int M, int E> __host__ __device__ constexpr int zline_smem_elems()
+{
+    return (M + 1) + ((M + 1) >> zline_pad<E>()) + 1;
+}
 
 #ifndef FFT3D_ROTCONST
 #define FFT3D_ROTCONST 1
@@ -537,12 +542,12 @@ __device__ __forceinline__ void zr2c_lines(const ZArgs &a, int64_t line0, unsign
 {
     typedef typename cvec<R>::T C;
     constexpr int NT = M / E;
-    constexpr int P = LineEx<C, NT>::kPadShift;
+    constexpr int P = zline_pad<E>();
     const int lt = threadIdx.x / NT;
     const int j = threadIdx.x % NT;
     const int64_t line = line0 + lt;
     const bool active = line < a.nlines;
-    LineEx<C, NT> ex{(C *)smem + lt * zline_smem_elems<M>()};
+    LineEx<C, NT, P> ex{(C *)smem + lt * zline_smem_elems<M, E>()};
 
     const C *in = (const C *)((const R *)a.real + (active ? line : 0) * a.real_pitch);
     C v[E];
@@ -605,12 +610,12 @@ __device__ __forceinline__ void zc2r_lines(const ZArgs &a, int64_t line0, unsign
 {
     typedef typename cvec<R>::T C;
     constexpr int NT = M / E;
-    constexpr int P = LineEx<C, NT>::kPadShift;
+    constexpr int P = zline_pad<E>();
     const int lt = threadIdx.x / NT;
     const int j = threadIdx.x % NT;
     const int64_t line = line0 + lt;
     const bool active = line < a.nlines;
-    LineEx<C, NT> ex{(C *)smem + lt * zline_smem_elems<M>()};
+    LineEx<C, NT, P> ex{(C *)smem + lt * zline_smem_elems<M, E>()};
 
     const int64_t l = active ? line : 0;
     const C *src;
