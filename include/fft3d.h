@@ -36,8 +36,12 @@
  * finished.  A plan may be used by one stream at a time (its scratch is
  * shared between calls); distinct plans are independent.
  *
- * Pointers must be device pointers aligned to one complex element
- * (8 bytes for FFT3D_F32, 16 bytes for FFT3D_F64), else FFT3D_ERR_ALIGN.
+ * Pointers must be aligned to one complex element (8 bytes for FFT3D_F32,
+ * 16 bytes for FFT3D_F64), else FFT3D_ERR_ALIGN, and point to device memory,
+ * except where a function says that host memory is accepted (the real input
+ * of an out-of-place fft3d_exec_r2c, the real output of
+ * fft3d_exec_c2r_overwrite).  A batched plan (fft3d_plan_create_batched)
+ * takes `batch` such arrays stored one after another.
  */
 #ifndef FFT3D_H
 #define FFT3D_H
@@ -129,8 +133,11 @@ int fft3d_exec_c2r(fft3d_plan plan, const void *in_cplx, void *out_real, void *s
  * here may be host memory the GPU can access directly (pinned / registered
  * host memory, or any system memory on a coherent CPU-GPU node): the first
  * and last passes then stream the field over the CPU-GPU link while the
- * strided passes stay in HBM.  With inout_cplx == out_real this is the
- * in-place inverse.
+ * strided passes stay in HBM.  Such a pass runs on a fixed, small grid (the
+ * link bounds it), so the strided passes of another plan on another stream
+ * can run beside it: several fields in flight on several streams overlap
+ * their link traffic with each other's work in HBM.  With inout_cplx ==
+ * out_real this is the in-place inverse.
  */
 int fft3d_exec_c2r_overwrite(fft3d_plan plan, void *inout_cplx, void *out_real, void *stream);
 
