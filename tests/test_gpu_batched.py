@@ -20,6 +20,8 @@ SHAPES = [
     (2, 1024, 32, 32),   # FP32 x-pass: pipelined kernel, one TMA map over both fields' rows
     (2, 8, 1024, 64),    # FP32 y-pass: pipelined kernel, even/odd row-pair TMA maps (odd pitch 33)
     (4, 6, 8, 12),
+    (3, 1, 16, 32),      # N0 = 1: no x-pass
+    (2, 32, 1, 16),      # N1 = 1: no y-pass
 ]
 
 
