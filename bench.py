@@ -140,6 +140,9 @@ def dist_setup(args):
     if world > 1:
         import torch.distributed as dist
         backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)  # one GPU per rank, bound before NCCL starts
         dist.init_process_group(backend=backend)
         pg = dist
     return world, rank, local, pg
