@@ -198,7 +198,10 @@ int bulk_mode(const fft3d_plan_s *p, const CLayout &src, int axis, int64_t w)
     const int64_t L = axis == 0 ? p->n0 : p->n1;
     if (!g.persistent || p->dtype != FFT3D_F32 || ((uintptr_t)src.main & 15) || L % (2 * kTmaBoxRows) != 0)
         return 0;
-    if (axis == 0) return (!src.split && (p->n1 * p->m1) % 2 == 0 && (p->n1 * p->m1) % w == 0) ? 1 : 0;
+    if (axis == 0)
+        return (!src.split && (p->n1 * p->m1) % 2 == 0 && (p->n1 * p->m1) % w == 0 && (!g.pair || p->n0 % 2 == 0))
+                   ? 1
+                   : 0;
     if (p->m % w != 0) return 0;
     if (src.split) return 1;  // main rows of pitch M (a multiple of W): 16-byte aligned
     return (p->m1 % 2 == 0) ? 1 : 2;
@@ -306,11 +309,13 @@ int run_colpass(fft3d_plan p, int kind, ColArgs a, int64_t tiles, int L, const v
     const CUtensorMap *mp = nullptr, *mp2 = nullptr;
     const int w = (int)(a.axis == 0 ? p->g0.per_block : p->g1.per_block);
     bool ok = true;
+    // a CTA pair (colpass_pair_kernel) reads rows of one parity: mode 1 maps row pairs
+    const int64_t pr = (a.axis == 0 ? p->g0.pair : p->g1.pair) ? 2 : 1;
     if (a.bulk == 1 && a.axis == 0) {
-        ok = tensor_map_2d(a.src.main, p->n1 * p->m1, p->nb0, p->n1 * p->m1, w, &map);
+        ok = tensor_map_2d(a.src.main, pr * p->n1 * p->m1, p->nb0 / pr, pr * p->n1 * p->m1, w, &map);
     } else if (a.bulk == 1) {
         const int64_t pitch = a.src.split ? p->m : p->m1;  // the split layout's k2 < M rows
-        ok = tensor_map_2d(a.src.main, pitch, p->nb0 * p->n1, pitch, w, &map);
+        ok = tensor_map_2d(a.src.main, pr * pitch, p->nb0 * p->n1 / pr, pr * pitch, w, &map);
     } else if (a.bulk == 2) {
         ok = tensor_map_2d(a.src.main, 2 * p->m1, p->nb0 * p->n1 / 2, 2 * p->m1, w, &map) &&
              tensor_map_2d(a.src.main, 2 * p->m1, p->nb0 * p->n1 / 2, 2 * p->m1, w + 2, &map2);
@@ -449,19 +454,6 @@ int inverse_pipeline(fft3d_plan p, const void *in, void *out, cudaStream_t st, d
     });
 }
 
-cudaError_t gen_line_tables(int dtype, int L, int E, void *dst)
-{
-    for (int s = 1; s < line_nstages(L, E); ++s) {
-        const size_t off = (size_t)line_tw_offset(L, E, s) * (dtype == FFT3D_F32 ? 8 : 16);
-        void *o = (char *)dst + off;
-        const int ns = line_ns(L, E, s), r = line_radix(L, E, s);
-        cudaError_t e = dtype == FFT3D_F32 ? twiddle_stage_launch_f32(o, ns, r, 0)
-                                           : twiddle_stage_launch_f64(o, ns, r, 0);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
 }  // namespace
 
 extern "C" {
@@ -507,8 +499,8 @@ int fft3d_plan_create_batched(fft3d_plan *out, int64_t batch, int64_t n0, int64_
         rc = FFT3D_ERR_CUDA;
         goto fail;
     }
-    if (!(f32 ? col_geom_f32((int)n0, &p->g0) : col_geom_f64((int)n0, &p->g0)) ||
-        !(f32 ? col_geom_f32((int)n1, &p->g1) : col_geom_f64((int)n1, &p->g1)) ||
+    if (!(f32 ? col_geom_f32((int)n0, 0, &p->g0) : col_geom_f64((int)n0, 0, &p->g0)) ||
+        !(f32 ? col_geom_f32((int)n1, 1, &p->g1) : col_geom_f64((int)n1, 1, &p->g1)) ||
         !(f32 ? z_geom_f32((int)p->m, &p->gz) : z_geom_f64((int)p->m, &p->gz))) {
         rc = FFT3D_ERR_SIZE;
         goto fail;
@@ -519,8 +511,8 @@ int fft3d_plan_create_batched(fft3d_plan *out, int64_t batch, int64_t n0, int64_
     p->fused = 0;  // opt-in: see fft3d_plan_set_fused
 
     {
-        const size_t s0 = align256((size_t)line_tw_size((int)n0, p->g0.E) * p->csize + 16);
-        const size_t s1 = align256((size_t)line_tw_size((int)n1, p->g1.E) * p->csize + 16);
+        const size_t s0 = align256((size_t)col_table_elems((int)n0, p->g0) * p->csize + 16);
+        const size_t s1 = align256((size_t)col_table_elems((int)n1, p->g1) * p->csize + 16);
         const size_t sz = align256((size_t)line_tw_size((int)p->m, p->gz.E) * p->csize + 16);
         const size_t sr = align256((size_t)p->m * p->csize);
         const size_t sf = p->fused_ok ? align256((size_t)line_tw_size((int)n1, p->gf.E) * p->csize + 16) : 0;
@@ -535,12 +527,12 @@ int fft3d_plan_create_batched(fft3d_plan *out, int64_t batch, int64_t n0, int64_
         p->twz = base + s0 + s1;
         p->rot = base + s0 + s1 + sz;
         p->tw1f = base + s0 + s1 + sz + sr;
-        if ((e = gen_line_tables(dtype, (int)n0, p->g0.E, base)) != cudaSuccess ||
-            (e = gen_line_tables(dtype, (int)n1, p->g1.E, base + s0)) != cudaSuccess ||
-            (e = gen_line_tables(dtype, (int)p->m, p->gz.E, base + s0 + s1)) != cudaSuccess ||
+        if ((e = write_col_tables(f32, (int)n0, p->g0, base, 0)) != cudaSuccess ||
+            (e = write_col_tables(f32, (int)n1, p->g1, base + s0, 0)) != cudaSuccess ||
+            (e = write_line_tables(f32, (int)p->m, p->gz.E, base + s0 + s1, 0)) != cudaSuccess ||
             (e = (f32 ? twiddle_rot_launch_f32 : twiddle_rot_launch_f64)(base + s0 + s1 + sz, (int)n2,
                                                                          (int)p->m, 0)) != cudaSuccess ||
-            (p->fused_ok && (e = gen_line_tables(dtype, (int)n1, p->gf.E, base + s0 + s1 + sz + sr)) != cudaSuccess)) {
+            (p->fused_ok && (e = write_line_tables(f32, (int)n1, p->gf.E, base + s0 + s1 + sz + sr, 0)) != cudaSuccess)) {
             rc = FFT3D_ERR_CUDA;
             goto fail;
         }

@@ -86,17 +86,6 @@ cudaError_t scratch_for_current_device(void **out)
     return cudaSuccess;
 }
 
-cudaError_t write_line_tables(bool f32, int L, int E, void *dst, cudaStream_t st)
-{
-    for (int s = 1; s < line_nstages(L, E); ++s) {
-        void *o = (char *)dst + (size_t)line_tw_offset(L, E, s) * (f32 ? 8 : 16);
-        cudaError_t e = f32 ? twiddle_stage_launch_f32(o, line_ns(L, E, s), line_radix(L, E, s), st)
-                            : twiddle_stage_launch_f64(o, line_ns(L, E, s), line_radix(L, E, s), st);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
 }  // namespace
 
 extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64_t n0, int64_t n1,
@@ -118,8 +107,8 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
         if (i0 < o0 + ob && o0 < i0 + ib) return FFT3D_ERR_LAYOUT;
     }
     PassGeom g0, g1, gz;
-    if (!(f32 ? col_geom_f32((int)n0, &g0) : col_geom_f64((int)n0, &g0)) ||
-        !(f32 ? col_geom_f32((int)n1, &g1) : col_geom_f64((int)n1, &g1)) ||
+    if (!(f32 ? col_geom_f32((int)n0, 0, &g0) : col_geom_f64((int)n0, 0, &g0)) ||
+        !(f32 ? col_geom_f32((int)n1, 1, &g1) : col_geom_f64((int)n1, 1, &g1)) ||
         !(f32 ? z_geom_f32((int)(n2 / 2), &gz) : z_geom_f64((int)(n2 / 2), &gz)))
         return FFT3D_ERR_SIZE;
 
@@ -136,8 +125,8 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
     unsigned *err_flag = (unsigned *)((char *)scratch + kTableBytes - 256);
 
     cudaError_t e;
-    if ((e = write_line_tables(f32, (int)n0, g0.E, tw0, st)) != cudaSuccess ||
-        (e = write_line_tables(f32, (int)n1, g1.E, tw1, st)) != cudaSuccess ||
+    if ((e = write_col_tables(f32, (int)n0, g0, tw0, st)) != cudaSuccess ||
+        (e = write_col_tables(f32, (int)n1, g1, tw1, st)) != cudaSuccess ||
         (e = write_line_tables(f32, (int)m, gz.E, twz, st)) != cudaSuccess ||
         (e = (f32 ? twiddle_rot_launch_f32 : twiddle_rot_launch_f64)(rot, (int)n2, (int)m, st)) != cudaSuccess)
         return FFT3D_ERR_CUDA;

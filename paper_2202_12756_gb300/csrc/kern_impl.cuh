@@ -40,6 +40,23 @@ template <typename R, int L> __host__ __device__ constexpr bool col_pipe()
 #endif
 }
 
+// float columns of 2048 points can run one tile of 16 columns per CTA pair
+// (colpass_pair_kernel), every row a 128-byte segment, instead of 8-column
+// tiles on one SM.  Measured on GB300 the pair makes the x-pass (rows one
+// N1 (N2/2+1) pitch apart, 2-17 MB) 20-37% faster and the y-pass (rows 4 KB
+// apart, where 64-byte segments of neighbouring rows share DRAM pages) 15%
+// slower, so it serves the axes in FFT3D_PAIR_AXES (bit 0: x-pass, bit 1:
+// y-pass).
+#ifndef FFT3D_PAIR_AXES
+#define FFT3D_PAIR_AXES 1
+#endif
+template <typename R, int L> __host__ __device__ constexpr bool col_pair()
+{
+    return col_pipe<R, L>() && L == 2048 && FFT3D_PAIR_AXES != 0;
+}
+__host__ __device__ constexpr bool pair_axis(int axis) { return axis >= 0 && ((FFT3D_PAIR_AXES >> axis) & 1) != 0; }
+constexpr int kPairW = 16;  // columns of a CTA-pair tile (128-byte float rows)
+
 template <typename R, int L> __host__ __device__ constexpr int col_E() { return col_pipe<R, L>() ? 32 : line_E(L); }
 
 // Columns per tile: one 128-byte segment per row (16 float2 or 8 double2),
@@ -64,7 +81,7 @@ template <typename R, int M> __host__ __device__ constexpr int z_LPB()
     return M / z_E<R, M>() >= FFT3D_Z_THREADS ? 1 : FFT3D_Z_THREADS / (M / z_E<R, M>());
 }
 
-template <typename R, int L> inline void col_geom_t(PassGeom *g)
+template <typename R, int L> inline void col_geom_t(PassGeom *g, int axis)
 {
     constexpr int W = col_W<R, L>();
     constexpr int E = col_E<R, L>();
@@ -72,8 +89,13 @@ template <typename R, int L> inline void col_geom_t(PassGeom *g)
     g->per_block = W;
     g->E = E;
     g->persistent = col_pipe<R, L>() ? 1 : 0;
+    g->pair = col_pair<R, L>() && pair_axis(axis) ? 1 : 0;
     typedef typename cvec<R>::T C;
-    if (col_pipe<R, L>())
+    if (g->pair) {
+        g->threads = kPairW * (L / 2 / E);
+        g->per_block = kPairW;
+        g->smem = pair_smem_bytes<L, E, kPairW>();
+    } else if (col_pipe<R, L>())
         g->smem = pipe_smem_bytes<R, L, E, W>();
     else
         g->smem = (size_t)L * W * sizeof(C);
@@ -92,8 +114,20 @@ template <typename R, int M> inline void z_geom_t(PassGeom *g)
 template <typename R, int L> inline cudaError_t col_prepare_t()
 {
     PassGeom g;
-    col_geom_t<R, L>(&g);
+    col_geom_t<R, L>(&g, -1);  // the one-SM kernels of the length
     cudaError_t e;
+    if constexpr (col_pair<R, L>()) {
+        constexpr int E = col_E<R, L>(), W = kPairW;
+        const void *const ks[4] = {(const void *)colpass_pair_kernel<R, L, E, W, false, false>,
+                                   (const void *)colpass_pair_kernel<R, L, E, W, true, false>,
+                                   (const void *)colpass_pair_kernel<R, L, E, W, false, true>,
+                                   (const void *)colpass_pair_kernel<R, L, E, W, true, true>};
+        for (const void *k : ks) {
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)pair_smem_bytes<L, E, W>());
+            if (e != cudaSuccess) return e;
+        }
+    }
     if constexpr (col_pipe<R, L>()) {
         constexpr int E = col_E<R, L>(), W = col_W<R, L>();
         const void *const ks[4] = {(const void *)colpass_pipe_kernel<R, L, E, W, false, false>,
@@ -167,13 +201,72 @@ inline int persistent_grid(K kernel, int threads, size_t smem, int64_t items, in
     return (int)(need < per_dev ? need : per_dev);
 }
 
+// Co-resident clusters of two CTAs of a pair kernel on the current device,
+// cached per (kernel, device), capped at `items` (one tile per cluster at a time).
+template <class K> inline int pair_clusters(K kernel, int threads, size_t smem, int64_t items)
+{
+    struct Entry {
+        const void *k;
+        int dev;
+        int clusters;
+    };
+    static Entry cache[16];
+    static std::mutex mu;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    int per_dev = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (const Entry &e : cache)
+            if (e.k == (const void *)kernel && e.dev == dev) per_dev = e.clusters;
+    }
+    if (per_dev <= 0) {
+        int sms = 0, nc = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaLaunchConfig_t cfg;
+        memset(&cfg, 0, sizeof(cfg));
+        cfg.gridDim = dim3((unsigned)(sms > 1 ? sms / 2 * 2 : 2), 1, 1);
+        cfg.blockDim = dim3((unsigned)threads, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        if (cudaOccupancyMaxActiveClusters(&nc, (const void *)kernel, &cfg) != cudaSuccess || nc <= 0) {
+            (void)cudaGetLastError();
+            nc = sms > 1 ? sms / 2 : 1;
+        }
+        per_dev = nc;
+        std::lock_guard<std::mutex> lock(mu);
+        for (Entry &e : cache)
+            if (e.k == nullptr) {
+                e = Entry{(const void *)kernel, dev, per_dev};
+                break;
+            }
+    }
+    return (int)(items < per_dev ? items : per_dev);
+}
+
 template <typename R, int L>
 inline cudaError_t col_launch_t(const ColArgs &a, int64_t tiles, const void *tw, const CUtensorMap *tmap,
                                 const CUtensorMap *tmap2, cudaStream_t st)
 {
     PassGeom g;
-    col_geom_t<R, L>(&g);
+    col_geom_t<R, L>(&g, a.axis);
     typedef const typename cvec<R>::T *TW;
+    if constexpr (col_pair<R, L>()) {
+        if (g.pair) {
+            constexpr int E = col_E<R, L>(), W = kPairW;
+            auto k = a.early ? (a.inverse ? colpass_pair_kernel<R, L, E, W, true, true>
+                                          : colpass_pair_kernel<R, L, E, W, false, true>)
+                             : (a.inverse ? colpass_pair_kernel<R, L, E, W, true, false>
+                                          : colpass_pair_kernel<R, L, E, W, false, false>);
+            const int grid = 2 * pair_clusters(k, g.threads, g.smem, tiles);
+            CUtensorMap map, map2;
+            if (tmap) map = *tmap;
+            else memset(&map, 0, sizeof(map));
+            if (tmap2) map2 = *tmap2;
+            else memset(&map2, 0, sizeof(map2));
+            k<<<grid, g.threads, g.smem, st>>>(a, (TW)tw, tiles, map, map2);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (col_pipe<R, L>()) {
         constexpr int E = col_E<R, L>(), W = col_W<R, L>();
         auto k = a.early ? (a.inverse ? colpass_pipe_kernel<R, L, E, W, true, true>
@@ -278,7 +371,7 @@ inline cudaError_t fused_launch_t(const FusedArgs &a, const void *tw_y, const vo
 
 #define FFT3D_FUSED_SHAPES(X) X(512, 256) X(768, 384) X(1024, 512) X(1536, 768) X(2048, 1024)
 
-#define FFT3D_CASE_COL_GEOM(L) case L: col_geom_t<R, L>(g); return true;
+#define FFT3D_CASE_COL_GEOM(L) case L: col_geom_t<R, L>(g, axis); return true;
 #define FFT3D_CASE_Z_GEOM(M) case M: z_geom_t<R, M>(g); return true;
 #define FFT3D_CASE_COL_PREP(L) case L: return col_prepare_t<R, L>();
 #define FFT3D_CASE_Z_PREP(M) case M: return z_prepare_t<R, M>();
@@ -288,7 +381,7 @@ inline cudaError_t fused_launch_t(const FusedArgs &a, const void *tw_y, const vo
 
 #define FFT3D_DEFINE_COL(SUF)                                                                   \
     namespace fft3d {                                                                           \
-    bool col_geom_##SUF(int L, PassGeom *g)                                                     \
+    bool col_geom_##SUF(int L, int axis, PassGeom *g)                                           \
     {                                                                                           \
         switch (L) { FFT3D_COL_LENGTHS(FFT3D_CASE_COL_GEOM) }                                   \
         return false;                                                                           \

@@ -23,14 +23,24 @@ struct PassGeom {
     int E;            // elements per thread (fixes the twiddle-table layout)
     int persistent;   // 1: grid-stride persistent kernel
     size_t smem;      // dynamic shared memory bytes
+    int pair = 0;     // column pass: 1 = a cluster of two CTAs per tile (colpass_pair_kernel)
 };
+
+// Twiddle table of a column pass, in complex elements: the line table of the
+// length, or for a CTA pair the line table of L/2 points followed by
+// W_L^j for j < L/2 / E (written by write_col_tables).
+inline int col_table_elems(int L, const PassGeom &g)
+{
+    return g.pair ? line_tw_size(L / 2, g.E) + L / 2 / g.E : line_tw_size(L, g.E);
+}
 
 // dtype-specific entry points, defined in kern_f32.cu / kern_f64.cu.
 // Each returns cudaSuccess or the launch error.  `prepare` raises the
 // dynamic shared-memory limit of the kernels a plan will use on the current
-// device; `geom` reports the launch geometry.
+// device; `geom` reports the launch geometry (of a column pass along `axis`:
+// 0 x-pass, 1 y-pass).
 #define FFT3D_DECLARE_LAUNCHERS(SUF, R)                                                              \
-    bool col_geom_##SUF(int L, PassGeom *g);                                                         \
+    bool col_geom_##SUF(int L, int axis, PassGeom *g);                                               \
     bool z_geom_##SUF(int M, PassGeom *g);                                                           \
     cudaError_t col_prepare_##SUF(int L);                                                            \
     cudaError_t z_prepare_##SUF(int M);                                                              \
@@ -45,6 +55,30 @@ struct PassGeom {
 
 FFT3D_DECLARE_LAUNCHERS(f32, float)
 FFT3D_DECLARE_LAUNCHERS(f64, double)
+
+// Writes the stage twiddles of an L-point line plan with E elements per
+// thread (FP64 sincospi, rounded once) to dst, on stream st.
+inline cudaError_t write_line_tables(bool f32, int L, int E, void *dst, cudaStream_t st)
+{
+    for (int s = 1; s < line_nstages(L, E); ++s) {
+        void *o = (char *)dst + (size_t)line_tw_offset(L, E, s) * (f32 ? 8 : 16);
+        cudaError_t e = f32 ? twiddle_stage_launch_f32(o, line_ns(L, E, s), line_radix(L, E, s), st)
+                            : twiddle_stage_launch_f64(o, line_ns(L, E, s), line_radix(L, E, s), st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Writes the twiddle table of an L-point column pass of geometry g
+// (col_table_elems(L, g) complex elements) to dst, on stream st.
+inline cudaError_t write_col_tables(bool f32, int L, const PassGeom &g, void *dst, cudaStream_t st)
+{
+    if (!g.pair) return write_line_tables(f32, L, g.E, dst, st);
+    cudaError_t e = write_line_tables(f32, L / 2, g.E, dst, st);
+    if (e != cudaSuccess) return e;
+    void *rot = (char *)dst + (size_t)line_tw_size(L / 2, g.E) * (f32 ? 8 : 16);
+    return f32 ? twiddle_rot_launch_f32(rot, L, L / 2 / g.E, st) : twiddle_rot_launch_f64(rot, L, L / 2 / g.E, st);
+}
 
 // Fused plane pass (float only): available for (N1, M) in
 // {(512, 256), (768, 384), (1024, 512), (1536, 768), (2048, 1024)}.

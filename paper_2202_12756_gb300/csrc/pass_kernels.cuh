@@ -463,6 +463,264 @@ colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
     cp_async_wait_all();
 }
 
+// ------------------------------------------------------------ column pairs
+// Columns too long for one SM to hold W = 16 of them (L = 2048 float: a
+// 256 KB tile) run on a cluster of two CTAs.  CTA r of the pair holds the
+// rows 2n + r (n < L/2) of the tile's 16 columns and computes their L/2-point
+// FFT Y_r (radix-2 decimation in time); the two halves meet in one radix-2
+// step, X[k] = Y_0[k] + W_L^k Y_1[k] and X[k + L/2] = Y_0[k] - W_L^k Y_1[k].
+// CTA 0 finishes k < L/4 and CTA 1 the rest: each sends the other half of its
+// Y into the partner's exchange buffer
+// through distributed shared memory (a thread's slots k = j + i NT are the
+// same in both CTAs, so thread (j, c) writes to thread (j, c) of the
+// partner), between two cluster barriers; each then applies W_L^k to the
+// half of Y_1 it holds.  Every row an SM reads or writes is
+// thus a 128-byte segment of 16 columns; at W = 8 (one SM per tile) the rows
+// were 64-byte segments, which HBM serves at about half the rate.
+// Staging as in colpass_pipe_kernel, with the row parity taking the place of
+// the row pair: a.bulk = 1 reads rows 2n + r through a map over row pairs
+// ([rows / 2][2 P], P the row pitch) at column x + r P; a.bulk = 2 (odd P) is
+// the even / odd map pair of that kernel, one per CTA.  A tile wait that runs
+// out is shared with the partner at the first cluster barrier, and both CTAs
+// leave together (neither may wait at a cluster barrier the other never
+// reaches), after a bounded wait for their own copies in flight.
+template <int L, int E, int W> __host__ __device__ constexpr size_t pair_smem_bytes()
+{
+    return (size_t)(L / 2) * (W + 2) * 8 + (size_t)split_rows<L / 2>() * W * 4 + 32 +
+           (size_t)(line_tw_size(L / 2, E) + L / 2 / E) * 8;
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;\n" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_count_x()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;\n" : "=r"(r));
+    return r;
+}
+// Address of this CTA's shared variable `a` in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_map(uint32_t a, uint32_t rank)
+{
+    uint32_t d;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(d) : "r"(a), "r"(rank));
+    return d;
+}
+__device__ __forceinline__ void cluster_st_u32(uint32_t a, unsigned v)
+{
+    asm volatile("st.shared::cluster.u32 [%0], %1;\n" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cluster_st_f2(uint32_t a, float2 v)
+{
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};\n" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+// All threads of both CTAs: shared-memory writes before it (local or remote)
+// are visible to every thread after it.
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+template <typename R, int L, int E, int W, bool INV, bool EARLY>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(W *(L / 2 / E), 1)
+colpass_pair_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64_t ntiles,
+                    const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap2)
+{
+    typedef typename cvec<R>::T C;
+    constexpr int LH = L / 2;  // rows per CTA
+    constexpr int NT = LH / E;
+    constexpr int H = E / 2;   // slots sent to / received from the partner
+    constexpr int NTW = line_tw_size(LH, E);
+    static_assert(sizeof(R) == 4 && W * sizeof(C) == 128, "float tiles of 128-byte rows");
+    static_assert(LH % kTmaBoxRows == 0 && E % 2 == 0, "staging layout");
+    static_assert(H * W * NT * sizeof(C) <= (size_t)split_rows<LH>() * W * sizeof(R), "receive buffer");
+    extern __shared__ __align__(1024) unsigned char pair_smem_raw[];
+    C *stage = (C *)pair_smem_raw;  // [LH][W] or, odd rows of a.bulk = 2, [LH][W + 2]
+    R *exbuf = (R *)(stage + LH * (W + 2));
+    uint64_t *mbar = (uint64_t *)(exbuf + split_rows<LH>() * W);
+    volatile unsigned *peer_bad = (volatile unsigned *)(mbar + 2);  // written by the partner
+    C *tws = (C *)(mbar + 4);  // line table of LH points, then W_L^j for j < NT
+    for (int i = threadIdx.x; i < NTW + NT; i += blockDim.x) tws[i] = __ldg(tw + i);
+    const uint32_t rank = cluster_ctarank();
+    const uint32_t peer = rank ^ 1u;
+    const int c = threadIdx.x % W;
+    const int j = threadIdx.x / W;
+    ColSplitEx<R, W> ex{exbuf, c};
+    const uint32_t mb = smem_u32(mbar);
+    if (threadIdx.x == 0) {
+        mbar_init(mb, 1);
+        mbar_fence_init();
+        *peer_bad = 0u;
+    }
+    // both CTAs have started (and initialised) before either addresses the other's shared memory
+    cluster_sync_all();
+    // the partner's receive slots for this thread and its flag word
+    const uint32_t peer_rx = cluster_map(smem_u32(exbuf), peer) + (uint32_t)threadIdx.x * (uint32_t)sizeof(C);
+    const uint32_t peer_flag = cluster_map(smem_u32((const void *)peer_bad), peer);
+    const C *rx = (const C *)exbuf + threadIdx.x;
+    constexpr uint32_t kRxStep = W * NT * sizeof(C);  // bytes between a thread's receive slots
+    uint32_t phase = 0;
+
+    // row pitch of the source tensor (elements) for a.bulk = 1
+    const int64_t P = a.axis == 0 ? a.n1 * (a.m + 1) : (a.src.split ? a.m : a.m + 1);
+    const bool odd_wide = a.bulk == 2 && rank == 1;  // staging rows W + 2 wide, column c at c + 1
+
+    auto fill = [&](int64_t tt, const C *sp, int64_t ss) -> int {
+        const int mode = tt < a.tiles_main ? a.bulk : 0;
+        if (mode) {
+            if (threadIdx.x == 0) {
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                int x, y0;  // y0: first row pair of the tile
+                if (a.axis == 0) {
+                    const int64_t b = (uint32_t)tt / (uint32_t)a.tiles_per_field;
+                    x = (int)((tt - b * a.tiles_per_field) * W);
+                    y0 = (int)(b * (a.n0 / 2));
+                } else {
+                    const int64_t k0 = tt / a.tiles_per_plane;
+                    x = (int)((tt - k0 * a.tiles_per_plane) * W);
+                    y0 = (int)(k0 * (a.n1 / 2));
+                }
+                if (mode == 1) {
+                    mbar_arrive_expect_tx(mb, (unsigned)(LH * W * sizeof(C)) + a.stall_tx);
+                    x += (int)(rank * P);
+#pragma unroll
+                    for (int b = 0; b < LH / kTmaBoxRows; ++b)
+                        tma_load_2d(smem_u32(stage + b * kTmaBoxRows * W), &tmap, x, y0 + b * kTmaBoxRows, mb);
+                } else if (rank == 0) {
+                    mbar_arrive_expect_tx(mb, (unsigned)(LH * W * sizeof(C)) + a.stall_tx);
+#pragma unroll
+                    for (int b = 0; b < LH / kTmaBoxRows; ++b)
+                        tma_load_2d(smem_u32(stage + b * kTmaBoxRows * W), &tmap, x, y0 + b * kTmaBoxRows, mb);
+                } else {
+                    mbar_arrive_expect_tx(mb, (unsigned)(LH * (W + 2) * sizeof(C)) + a.stall_tx);
+#pragma unroll
+                    for (int b = 0; b < LH / kTmaBoxRows; ++b)
+                        tma_load_2d(smem_u32(stage + b * kTmaBoxRows * (W + 2)), &tmap2, x + (int)a.m,
+                                    y0 + b * kTmaBoxRows, mb);
+                }
+            }
+        } else {
+            const C *sj = sp + (int64_t)(2 * j + (int)rank) * ss;
+            const int64_t sstep = (int64_t)2 * NT * ss;
+#pragma unroll
+            for (int i = 0; i < E; ++i) cp_async_8(stage + (j + i * NT) * W + c, sj + i * sstep);
+            cp_async_commit();
+        }
+        return mode;
+    };
+
+    int64_t t = cluster_id_x();
+    const int64_t tstep = cluster_count_x();
+    C *sp = nullptr, *dp = nullptr;
+    int64_t ss = 0, ds = 0;
+    bool valid = t < ntiles && col_decode<C, W>(a, t, c, sp, ss, dp, ds);
+    int mode = t < ntiles ? fill(t, sp, ss) : 0;
+    while (t < ntiles) {
+        const int64_t tn = t + tstep;
+        C *spn = nullptr, *dpn = nullptr;
+        int64_t ssn = 0, dsn = 0;
+        const bool validn = tn < ntiles && col_decode<C, W>(a, tn, c, spn, ssn, dpn, dsn);
+
+        bool ok = true;
+        if (mode) ok = mbar_wait_bounded(mb, phase, a.stage_polls);
+        else cp_async_wait_all();
+        const int bad = __syncthreads_or(!ok);
+        int moden = 0;
+        C v[E];
+        if (!bad) {
+            if (mode) phase ^= 1u;
+            const int rs = (mode && odd_wide) ? W + 2 : W;
+            const C *base = stage + j * rs + c + ((mode && odd_wide) ? 1 : 0);
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                v[i] = base[i * NT * rs];
+                if (INV) v[i] = cswap(v[i]);
+            }
+            auto next = [&]() {
+                if (tn < ntiles) moden = fill(tn, spn, ssn);
+            };
+            if constexpr (EARLY) {
+                __syncthreads();
+                next();
+                line_fft<R, LH, E, true>(v, j, tws, ex);
+            } else {
+                line_fft<R, LH, E, true>(v, j, tws, ex, next);
+            }
+            if (rank == 1) {  // W_L^k on the half of Y_1 this CTA keeps (k = j + (H + i) NT)
+                const C rot_j = tws[NTW + j];  // W_L^j
+                static_for<0, H>([&](auto II) {
+                    constexpr int i = decltype(II)::value;
+                    constexpr CtCosSin w = ct_cossin_pi(-(long long)(H + i), E);
+                    v[H + i] = cmul(v[H + i], cmul(rot_j, cmake<C>(R(w.c), R(w.s))));
+                });
+            }
+        }
+        // first cluster barrier: both CTAs are done with their exchange
+        // buffers, and each knows whether the other's tile wait ran out
+        if (threadIdx.x == 0) cluster_st_u32(peer_flag, (unsigned)bad);
+        cluster_sync_all();
+        if (bad || *peer_bad) {
+            if (threadIdx.x == 0 && bad) atomicOr(a.err, 1u);
+            if (mode && !ok) mbar_wait_bounded(mb, phase, a.stage_polls);  // this tile's copies
+            else if (moden) mbar_wait_bounded(mb, phase, a.stage_polls);   // the next tile's copies
+            cp_async_wait_all();
+            return;
+        }
+        if (rank == 0) {
+#pragma unroll
+            for (int i = 0; i < H; ++i) cluster_st_f2(peer_rx + i * kRxStep, v[H + i]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < H; ++i) cluster_st_f2(peer_rx + i * kRxStep, v[i]);
+        }
+        cluster_sync_all();
+        if (valid) {
+            const int64_t dstep = (int64_t)NT * ds;
+            const int64_t dhalf = (int64_t)LH * ds;
+            // rank 0: k = j + i NT (i < H),   own Y_0, received Y_1
+            // rank 1: k = j + (H + i) NT,     received Y_0, own Y_1
+            // each CTA applies W_L^k = W_L^j exp(-pi i slot / E) to its H values of Y_1
+            C *dj = dp + (int64_t)(j + (int)rank * H * NT) * ds;
+            // rank 0 applies W_L^k to the half of Y_1 it receives (k = j + i NT)
+            const C rot_j = tws[NTW + j];
+            static_for<0, H>([&](auto II) {
+                constexpr int i = decltype(II)::value;
+                constexpr CtCosSin w = ct_cossin_pi(-(long long)i, E);
+                C u = rx[i * W * NT];
+                if (rank == 0) u = cmul(u, cmul(rot_j, cmake<C>(R(w.c), R(w.s))));
+                const C y0 = rank == 0 ? v[i] : u;
+                const C y1 = rank == 0 ? u : v[H + i];
+                C lo = cadd(y0, y1), hi = csub(y0, y1);
+                if (INV) {
+                    lo = cswap(lo);
+                    hi = cswap(hi);
+                }
+                store_out(dj + i * dstep, lo);
+                store_out(dj + i * dstep + dhalf, hi);
+            });
+        }
+        t = tn;
+        valid = validn;
+        mode = moden;
+        sp = spn;
+        ss = ssn;
+        dp = dpn;
+        ds = dsn;
+    }
+    cp_async_wait_all();
+    cluster_sync_all();  // no CTA leaves while its partner may still address its shared memory
+}
+
 // ------------------------------------------------------------ z pass
 struct ZArgs {
     const void *real;     // real lines (read by r2c, written by c2r)

@@ -59,14 +59,17 @@ def test_plans_without_fused_pass_report_no_error():
     assert plan.status() == 0
 
 
-@pytest.mark.parametrize("shape", [(1024, 16, 32), (8, 1024, 64)], ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("shape", [(1024, 16, 32), (8, 1024, 64), (2048, 16, 32), (8, 2048, 64)],
+                         ids=lambda s: "x".join(map(str, s)))
 def test_pipelined_tile_wait_reports_and_recovers(shape):
     """The pipelined column kernel waits on an mbarrier for the TMA copies of
     each tile.  With the test hook every tile wait expects 16 bytes more than
     its copies deliver, so it runs out after a short bound: the blocks stop,
     the flag is reported once, and the same plan then computes correctly.
     (1024, 16, 32): x-pass over whole rows; (8, 1024, 64): y-pass with the
-    even/odd row-pair copies of an odd row pitch.)"""
+    even/odd row-pair copies of an odd row pitch.  The 2048-point shapes run
+    the two-CTA kernel, whose CTAs share the outcome of their waits at a
+    cluster barrier and leave together.)"""
     import torch
     import paper_2202_12756_gb300 as fft3d
     plan = fft3d.Plan(shape, torch.float32)

@@ -228,6 +228,21 @@ def test_tma_staged_column_passes(shape):
         check_pair(shape, "f32", inplace, seed=9)
 
 
+@pytest.mark.parametrize("shape", [(2048, 64, 64), (2048, 24, 24), (32, 2048, 64), (3, 2048, 192)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_cta_pair_column_passes(shape):
+    """Float columns of 2048 points run on clusters of two CTAs, each holding
+    one row parity of a 16-column tile (1024-point FFTs, then one radix-2
+    step across the pair through distributed shared memory).  Shapes: x-pass
+    tiles staged by TMA from the row-pair map (2048 x 64 x 64: 64 * 33
+    columns, 132 full tiles), per-element copies with a ragged last tile
+    (24 * 13 = 312 columns), y-pass even / odd row maps (in place, odd pitch
+    33 or 97) or the row-pair map over the split layout (out of place); both
+    directions, element by element against the oracle."""
+    for inplace in (False, True):
+        check_pair(shape, "f32", inplace, seed=17)
+
+
 @pytest.mark.parametrize("name", ["f64", "f32"])
 def test_cuda_graph_capture_and_replay(name):
     """The exec calls only enqueue work on the caller's stream, so a forward +
