@@ -469,21 +469,27 @@ colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
 // rows 2n + r (n < L/2) of the tile's 16 columns and computes their L/2-point
 // FFT Y_r (radix-2 decimation in time); the two halves meet in one radix-2
 // step, X[k] = Y_0[k] + W_L^k Y_1[k] and X[k + L/2] = Y_0[k] - W_L^k Y_1[k].
-// CTA 0 finishes k < L/4 and CTA 1 the rest: each sends the other half of its
-// Y into the partner's exchange buffer
-// through distributed shared memory (a thread's slots k = j + i NT are the
-// same in both CTAs, so thread (j, c) writes to thread (j, c) of the
-// partner), between two cluster barriers; each then applies W_L^k to the
-// half of Y_1 it holds.  Every row an SM reads or writes is
-// thus a 128-byte segment of 16 columns; at W = 8 (one SM per tile) the rows
-// were 64-byte segments, which HBM serves at about half the rate.
+// CTA 0 finishes k < L/4 and CTA 1 the rest, so each sends the other half of
+// its Y into the partner's exchange buffer through distributed shared memory
+// (a thread's slots k = j + i NT are the same in both CTAs: thread (j, c)
+// writes to thread (j, c) of the partner); each CTA applies W_L^k to the half
+// of Y_1 it ends up with.  Every row an SM reads or writes is thus a 128-byte
+// segment of 16 columns; at W = 8 (one SM per tile) rows are 64-byte
+// segments, which HBM serves at about half the rate at large row pitches.
+// The exchange runs on mbarriers, not cluster barriers: once its transform
+// is done with the exchange buffer, a CTA arms its receive barrier for the
+// partner's 64 KB and tells the partner, by one remote arrival on the
+// partner's "free" barrier, that it may write; the partner's st.async stores
+// complete on the receive barrier.  (Two cluster barriers per tile instead,
+// each a release by every thread, measured 2% slower.)  Every wait is
+// bounded: a CTA whose wait runs out raises *a.err and leaves its loop, its
+// partner's next wait then runs out as well, and both wait (bounded) for the
+// copies and stores still in flight into their shared memory and meet at a
+// final cluster barrier, so no CTA leaves while the other may address it.
 // Staging as in colpass_pipe_kernel, with the row parity taking the place of
 // the row pair: a.bulk = 1 reads rows 2n + r through a map over row pairs
 // ([rows / 2][2 P], P the row pitch) at column x + r P; a.bulk = 2 (odd P) is
-// the even / odd map pair of that kernel, one per CTA.  A tile wait that runs
-// out is shared with the partner at the first cluster barrier, and both CTAs
-// leave together (neither may wait at a cluster barrier the other never
-// reaches), after a bounded wait for their own copies in flight.
+// the even / odd map pair of that kernel, one per CTA.
 template <int L, int E, int W> __host__ __device__ constexpr size_t pair_smem_bytes()
 {
     return (size_t)(L / 2) * (W + 2) * 8 + (size_t)split_rows<L / 2>() * W * 4 + 32 +
@@ -515,20 +521,43 @@ __device__ __forceinline__ uint32_t cluster_map(uint32_t a, uint32_t rank)
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(d) : "r"(a), "r"(rank));
     return d;
 }
-__device__ __forceinline__ void cluster_st_u32(uint32_t a, unsigned v)
-{
-    asm volatile("st.shared::cluster.u32 [%0], %1;\n" ::"r"(a), "r"(v) : "memory");
-}
-__device__ __forceinline__ void cluster_st_f2(uint32_t a, float2 v)
-{
-    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};\n" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
-}
 // All threads of both CTAs: shared-memory writes before it (local or remote)
 // are visible to every thread after it.
 __device__ __forceinline__ void cluster_sync_all()
 {
     asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
     asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+// One arrival on an mbarrier of another CTA of the cluster (cluster address),
+// ordered after this thread's earlier memory accesses.
+__device__ __forceinline__ void mbar_remote_arrive(uint32_t a)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];\n" ::"r"(a) : "memory");
+}
+// Asynchronous 8-byte store into another CTA's shared memory, completing
+// (8 bytes of transaction count) on that CTA's mbarrier `mb`.
+__device__ __forceinline__ void st_async_f2(uint32_t a, float2 v, uint32_t mb)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];\n" ::"r"(a),
+                 "f"(v.x), "f"(v.y), "r"(mb)
+                 : "memory");
+}
+// Bounded wait for a phase completed from another CTA of the cluster.
+__device__ __forceinline__ bool mbar_wait_cluster_bounded(uint32_t mb, uint32_t parity, long long limit)
+{
+    for (long long n = 0; n < limit; ++n) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(mb), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        __nanosleep(32);
+    }
+    return false;
 }
 
 template <typename R, int L, int E, int W, bool INV, bool EARLY>
@@ -544,11 +573,12 @@ colpass_pair_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
     static_assert(sizeof(R) == 4 && W * sizeof(C) == 128, "float tiles of 128-byte rows");
     static_assert(LH % kTmaBoxRows == 0 && E % 2 == 0, "staging layout");
     static_assert(H * W * NT * sizeof(C) <= (size_t)split_rows<LH>() * W * sizeof(R), "receive buffer");
+    static_assert(line_nstages(LH, E) >= 2, "the transform must end its exchange-buffer use on a barrier");
     extern __shared__ __align__(1024) unsigned char pair_smem_raw[];
     C *stage = (C *)pair_smem_raw;  // [LH][W] or, odd rows of a.bulk = 2, [LH][W + 2]
     R *exbuf = (R *)(stage + LH * (W + 2));
+    // mbarriers: the tile's staging copies, the partner's data, the partner's exchange buffer free
     uint64_t *mbar = (uint64_t *)(exbuf + split_rows<LH>() * W);
-    volatile unsigned *peer_bad = (volatile unsigned *)(mbar + 2);  // written by the partner
     C *tws = (C *)(mbar + 4);  // line table of LH points, then W_L^j for j < NT
     for (int i = threadIdx.x; i < NTW + NT; i += blockDim.x) tws[i] = __ldg(tw + i);
     const uint32_t rank = cluster_ctarank();
@@ -556,20 +586,23 @@ colpass_pair_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
     const int c = threadIdx.x % W;
     const int j = threadIdx.x / W;
     ColSplitEx<R, W> ex{exbuf, c};
-    const uint32_t mb = smem_u32(mbar);
+    const uint32_t mb = smem_u32(mbar), mb_rx = smem_u32(mbar + 1), mb_free = smem_u32(mbar + 2);
     if (threadIdx.x == 0) {
         mbar_init(mb, 1);
+        mbar_init(mb_rx, 1);
+        mbar_init(mb_free, 1);
         mbar_fence_init();
-        *peer_bad = 0u;
     }
     // both CTAs have started (and initialised) before either addresses the other's shared memory
     cluster_sync_all();
-    // the partner's receive slots for this thread and its flag word
+    // the partner's receive slots for this thread and its mbarriers
     const uint32_t peer_rx = cluster_map(smem_u32(exbuf), peer) + (uint32_t)threadIdx.x * (uint32_t)sizeof(C);
-    const uint32_t peer_flag = cluster_map(smem_u32((const void *)peer_bad), peer);
+    const uint32_t peer_mb_rx = cluster_map(mb_rx, peer), peer_mb_free = cluster_map(mb_free, peer);
     const C *rx = (const C *)exbuf + threadIdx.x;
     constexpr uint32_t kRxStep = W * NT * sizeof(C);  // bytes between a thread's receive slots
-    uint32_t phase = 0;
+    uint32_t phase = 0;  // staging barrier
+    uint32_t xph = 0;    // receive and free barriers (one phase per tile)
+    bool failed = false, stage_pending = false, rx_pending = false;
 
     // row pitch of the source tensor (elements) for a.bulk = 1
     const int64_t P = a.axis == 0 ? a.n1 * (a.m + 1) : (a.src.split ? a.m : a.m + 1);
@@ -665,33 +698,46 @@ colpass_pair_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
                 });
             }
         }
-        // first cluster barrier: both CTAs are done with their exchange
-        // buffers, and each knows whether the other's tile wait ran out
-        if (threadIdx.x == 0) cluster_st_u32(peer_flag, (unsigned)bad);
-        cluster_sync_all();
-        if (bad || *peer_bad) {
-            if (threadIdx.x == 0 && bad) atomicOr(a.err, 1u);
-            if (mode && !ok) mbar_wait_bounded(mb, phase, a.stage_polls);  // this tile's copies
-            else if (moden) mbar_wait_bounded(mb, phase, a.stage_polls);   // the next tile's copies
-            cp_async_wait_all();
-            return;
+        // A wait that runs out ends this CTA's loop; the partner's next
+        // wait then runs out too, and both meet at the final barrier.
+        if (bad) {
+            failed = true;
+            stage_pending = mode != 0;
+            break;
+        }
+        stage_pending = moden != 0;
+        // every thread is past its last read of the exchange buffer (the
+        // transform ended on a barrier): arm the receive barrier, then
+        // let the partner write
+        if (threadIdx.x == 0) {
+            mbar_arrive_expect_tx(mb_rx, (unsigned)(H * W * NT * sizeof(C)));
+            mbar_remote_arrive(peer_mb_free);
+        }
+        rx_pending = true;
+        if (__syncthreads_or(!mbar_wait_cluster_bounded(mb_free, xph, a.stage_polls))) {
+            failed = true;
+            break;
         }
         if (rank == 0) {
 #pragma unroll
-            for (int i = 0; i < H; ++i) cluster_st_f2(peer_rx + i * kRxStep, v[H + i]);
+            for (int i = 0; i < H; ++i) st_async_f2(peer_rx + i * kRxStep, v[H + i], peer_mb_rx);
         } else {
 #pragma unroll
-            for (int i = 0; i < H; ++i) cluster_st_f2(peer_rx + i * kRxStep, v[i]);
+            for (int i = 0; i < H; ++i) st_async_f2(peer_rx + i * kRxStep, v[i], peer_mb_rx);
         }
-        cluster_sync_all();
+        if (__syncthreads_or(!mbar_wait_cluster_bounded(mb_rx, xph, a.stage_polls))) {
+            failed = true;
+            break;
+        }
+        rx_pending = false;
+        stage_pending = false;
+        xph ^= 1u;
         if (valid) {
             const int64_t dstep = (int64_t)NT * ds;
             const int64_t dhalf = (int64_t)LH * ds;
-            // rank 0: k = j + i NT (i < H),   own Y_0, received Y_1
-            // rank 1: k = j + (H + i) NT,     received Y_0, own Y_1
-            // each CTA applies W_L^k = W_L^j exp(-pi i slot / E) to its H values of Y_1
+            // rank 0: k = j + i NT (i < H), own Y_0, received Y_1 (times W_L^k here)
+            // rank 1: k = j + (H + i) NT,   received Y_0, own W_L^k Y_1
             C *dj = dp + (int64_t)(j + (int)rank * H * NT) * ds;
-            // rank 0 applies W_L^k to the half of Y_1 it receives (k = j + i NT)
             const C rot_j = tws[NTW + j];
             static_for<0, H>([&](auto II) {
                 constexpr int i = decltype(II)::value;
@@ -716,6 +762,11 @@ colpass_pair_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
         ss = ssn;
         dp = dpn;
         ds = dsn;
+    }
+    if (failed) {
+        if (threadIdx.x == 0) atomicOr(a.err, 1u);
+        if (stage_pending) mbar_wait_bounded(mb, phase, a.stage_polls);      // staging copies in flight
+        if (rx_pending) mbar_wait_cluster_bounded(mb_rx, xph, a.stage_polls);  // the partner's stores
     }
     cp_async_wait_all();
     cluster_sync_all();  // no CTA leaves while its partner may still address its shared memory
