@@ -50,10 +50,14 @@ template <typename R, int L> __host__ __device__ constexpr bool col_pipe()
 #ifndef FFT3D_PAIR_AXES
 #define FFT3D_PAIR_AXES 1
 #endif
+// (At 1536 points the pair, with 768-point halves, measured 19% slower than
+// the one-tile kernel, whose 1024-thread blocks already read 128-byte rows.)
 template <typename R, int L> __host__ __device__ constexpr bool col_pair()
 {
-    return col_pipe<R, L>() && L == 2048 && FFT3D_PAIR_AXES != 0;
+    return sizeof(R) == 4 && L == 2048 && FFT3D_PAIR_AXES != 0;
 }
+// elements per thread of a pair's half-length transform (radix 32 x 32)
+template <int L> __host__ __device__ constexpr int pair_E() { return 32; }
 __host__ __device__ constexpr bool pair_axis(int axis) { return axis >= 0 && ((FFT3D_PAIR_AXES >> axis) & 1) != 0; }
 constexpr int kPairW = 16;  // columns of a CTA-pair tile (128-byte float rows)
 
@@ -91,11 +95,18 @@ template <typename R, int L> inline void col_geom_t(PassGeom *g, int axis)
     g->persistent = col_pipe<R, L>() ? 1 : 0;
     g->pair = col_pair<R, L>() && pair_axis(axis) ? 1 : 0;
     typedef typename cvec<R>::T C;
-    if (g->pair) {
-        g->threads = kPairW * (L / 2 / E);
-        g->per_block = kPairW;
-        g->smem = pair_smem_bytes<L, E, kPairW>();
-    } else if (col_pipe<R, L>())
+    if constexpr (col_pair<R, L>()) {
+        if (g->pair) {
+            constexpr int PE = pair_E<L>();
+            g->threads = kPairW * (L / 2 / PE);
+            g->per_block = kPairW;
+            g->E = PE;
+            g->persistent = 1;
+            g->smem = pair_smem_bytes<L, PE, kPairW>();
+            return;
+        }
+    }
+    if (col_pipe<R, L>())
         g->smem = pipe_smem_bytes<R, L, E, W>();
     else
         g->smem = (size_t)L * W * sizeof(C);
@@ -117,7 +128,7 @@ template <typename R, int L> inline cudaError_t col_prepare_t()
     col_geom_t<R, L>(&g, -1);  // the one-SM kernels of the length
     cudaError_t e;
     if constexpr (col_pair<R, L>()) {
-        constexpr int E = col_E<R, L>(), W = kPairW;
+        constexpr int E = pair_E<L>(), W = kPairW;
         const void *const ks[4] = {(const void *)colpass_pair_kernel<R, L, E, W, false, false>,
                                    (const void *)colpass_pair_kernel<R, L, E, W, true, false>,
                                    (const void *)colpass_pair_kernel<R, L, E, W, false, true>,
@@ -252,7 +263,7 @@ inline cudaError_t col_launch_t(const ColArgs &a, int64_t tiles, const void *tw,
     typedef const typename cvec<R>::T *TW;
     if constexpr (col_pair<R, L>()) {
         if (g.pair) {
-            constexpr int E = col_E<R, L>(), W = kPairW;
+            constexpr int E = pair_E<L>(), W = kPairW;
             auto k = a.early ? (a.inverse ? colpass_pair_kernel<R, L, E, W, true, true>
                                           : colpass_pair_kernel<R, L, E, W, false, true>)
                              : (a.inverse ? colpass_pair_kernel<R, L, E, W, true, false>

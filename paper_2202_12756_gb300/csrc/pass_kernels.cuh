@@ -786,26 +786,42 @@ struct ZArgs {
 
 // Elements per thread of a z-pass line: the default plan of the length (16,
 // or 24 for 3 * 2^k; radix 16 first).  32 elements (radix 32 first, one
-// exchange fewer) doubles the registers of a thread and, measured on GB300
-// at M = 512, halves the resident warps and runs 25% slower.
+// exchange fewer, and one warp per line up to M = 1024) doubles the registers
+// of a thread; measured on GB300 it halves the resident warps and runs 25%
+// slower at M = 512, and at M = 1024 (150-170 registers, one block per SM)
+// 45% slower.
 template <typename R, int M> __host__ __device__ constexpr int z_E() { return line_E(M); }
 
 // Per-line shared-memory exchange with one padding slot every 2^P elements:
 // P = 4 makes the stride-16 writes of a radix-16 first stage conflict-free,
 // P = 3 the stride-24 writes of a radix-24 one.  Indices arrive padded
 // (i + (i >> P), see pad_row).
+// A line of more than one warp (M = 1024: 64 threads) syncs only its own
+// warps, on named barrier `bar` (1..15) when bar > 0, else the whole block.
+// Measured on GB300 at M = 1024 against block barriers: the C2R z-pass 9%
+// and the R2C one 1.5% faster.
 template <typename C, int NT, int P> struct LineEx {
     static constexpr bool kSplit = false;
     static constexpr int kPadShift = P;
     C *sm;
+    int bar;
     __device__ __forceinline__ void put(int pi, C v) { sm[pi] = v; }
     __device__ __forceinline__ C get(int pi) const { return sm[pi]; }
     __device__ __forceinline__ void sync() const
     {
-        if (NT <= 32) __syncwarp();
-        else __syncthreads();
+        if (NT <= 32) {
+            __syncwarp();
+        } else if (bar > 0) {
+            asm volatile("bar.sync %0, %1;\n" ::"r"(bar), "n"(NT) : "memory");
+        } else {
+            __syncthreads();
+        }
     }
 };
+template <int NT, int LPB> __device__ __forceinline__ int line_bar(int lt)
+{
+    return (NT > 32 && LPB > 1 && LPB < 16) ? 1 + lt : 0;
+}
 
 template <int E> __host__ __device__ constexpr int zline_pad() { return E % 3 == 0 ? 3 : 4; }
 template <int M, int E> __host__ __device__ constexpr int zline_smem_elems()
@@ -856,7 +872,7 @@ __device__ __forceinline__ void zr2c_lines(const ZArgs &a, int64_t line0, unsign
     const int j = threadIdx.x % NT;
     const int64_t line = line0 + lt;
     const bool active = line < a.nlines;
-    LineEx<C, NT, P> ex{(C *)smem + lt * zline_smem_elems<M, E>()};
+    LineEx<C, NT, P> ex{(C *)smem + lt * zline_smem_elems<M, E>(), line_bar<NT, LPB>(lt)};
 
     const C *in = (const C *)((const R *)a.real + (active ? line : 0) * a.real_pitch);
     C v[E];
@@ -924,7 +940,7 @@ __device__ __forceinline__ void zc2r_lines(const ZArgs &a, int64_t line0, unsign
     const int j = threadIdx.x % NT;
     const int64_t line = line0 + lt;
     const bool active = line < a.nlines;
-    LineEx<C, NT, P> ex{(C *)smem + lt * zline_smem_elems<M, E>()};
+    LineEx<C, NT, P> ex{(C *)smem + lt * zline_smem_elems<M, E>(), line_bar<NT, LPB>(lt)};
 
     const int64_t l = active ? line : 0;
     const C *src;
