@@ -906,7 +906,7 @@ __device__ __forceinline__ void zr2c_lines(const ZArgs &a, int64_t line0, unsign
         });
     } else {
         constexpr bool LR = pad_linear_reads<P>(NT);
-        constexpr bool LREV = NT % (1 << P) == 0;  // M - j - i NT stays linear in i
+        constexpr bool LREV = P < 0 || NT % (1 << P) == 0;  // M - j - i NT stays linear in i
 #pragma unroll
         for (int i = 0; i < E; ++i) ex.put(pad_row<P, LR>(j, i * NT), v[i]);
         ex.sync();
@@ -990,7 +990,7 @@ __device__ __forceinline__ void zc2r_lines(const ZArgs &a, int64_t line0, unsign
         });
     } else {
         constexpr bool LR = pad_linear_reads<P>(NT);
-        constexpr bool LREV = NT % (1 << P) == 0;
+        constexpr bool LREV = P < 0 || NT % (1 << P) == 0;
 #pragma unroll
         for (int i = 0; i < E; ++i) ex.put(pad_row<P, LR>(j, i * NT), v[i]);
         if (j == 0) ex.put(pad_row<P, true>(M, 0), active ? (CG ? load_cg(nyq) : *nyq) : cmake<C>(R(0), R(0)));
@@ -1019,8 +1019,19 @@ __device__ __forceinline__ void zc2r_lines(const ZArgs &a, int64_t line0, unsign
 // walks the line groups (the host-memory form, bound by the CPU-GPU link).
 // Two instances because the loop slows the one-pass form down (up to 20%
 // measured for the C2R lines on GB300).
+// Minimum resident blocks in the launch bounds of the R2C z kernel: 1 (an
+// explicit floor, which changes the compiler's register budget) for float
+// lines of 3 * 2^k >= 384 points, else 0 (no floor).  Measured on GB300 the
+// floor cuts registers 127 -> 107 (M = 768) and 123 -> 95 (M = 384), and
+// the pass time by 7-8% (1536^3: 5.77 -> 5.33 ms); for M = 96 it is 1%
+// slower, and for the C2R kernel, or powers of two, it raises registers.
+template <typename R, int M, int E> __host__ __device__ constexpr int zr2c_minb()
+{
+    return sizeof(R) == 4 && E == 24 && M >= 384 ? 1 : 0;
+}
+
 template <typename R, int M, int E, int LPB, bool LOOP>
-__global__ void __launch_bounds__(LPB *(M / E))
+__global__ void __launch_bounds__(LPB *(M / E), zr2c_minb<R, M, E>())
 zpass_r2c_kernel(ZArgs a, const typename cvec<R>::T *__restrict__ tw,
                  const typename cvec<R>::T *__restrict__ rot)
 {
