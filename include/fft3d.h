@@ -207,9 +207,11 @@ int fft3d_plan_set_fused(fft3d_plan plan, int enable);
  * Device-side error flag of the plan's kernels that wait: the fused plane
  * pass (see fft3d_plan_set_fused), whose blocks wait on per-plane counters,
  * and the pipelined FP32 column passes, whose blocks wait on an mbarrier for
- * the TMA copies of their next tile.  Each such wait is bounded; a wait that
- * runs out makes the waiting blocks stop early (the output is then invalid)
- * and sets this flag.  fft3d_plan_status synchronises the device, stores the
+ * the TMA copies of their next tile (2048-point x-passes run each tile on a
+ * cluster of two blocks, which also wait on mbarriers for each other's half
+ * of the last radix-2 step).  Each such wait is bounded; a wait that runs out
+ * makes the waiting blocks (both blocks of a cluster) stop early (the output
+ * is then invalid) and sets this flag.  fft3d_plan_status synchronises the device, stores the
  * flag (0 or 1) in *device_error and clears it.
  */
 int fft3d_plan_status(fft3d_plan plan, int *device_error);
