@@ -67,9 +67,10 @@ def test_pipelined_tile_wait_reports_and_recovers(shape):
     its copies deliver, so it runs out after a short bound: the blocks stop,
     the flag is reported once, and the same plan then computes correctly.
     (1024, 16, 32): x-pass over whole rows; (8, 1024, 64): y-pass with the
-    even/odd row-pair copies of an odd row pitch.  The 2048-point shapes run
-    the two-CTA kernel, whose CTAs share the outcome of their waits at a
-    cluster barrier and leave together.)"""
+    even/odd row-pair copies of an odd row pitch; (2048, 16, 32): the x-pass
+    on clusters of two CTAs, which meet at a final cluster barrier whichever
+    of their waits runs out; (8, 2048, 64): the 2048-point y-pass on one SM
+    per 8-column tile.)"""
     import torch
     import paper_2202_12756_gb300 as fft3d
     plan = fft3d.Plan(shape, torch.float32)
