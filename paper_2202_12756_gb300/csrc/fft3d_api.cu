@@ -226,6 +226,7 @@ ColArgs ypass_args(const fft3d_plan_s *p, CLayout src, CLayout dst, int inverse,
     a.bulk = bulk_mode(p, src, 1, w);
     a.err = p->status;
     a.tiles_per_field = 1;
+    a.pf_stride = 0;
     // early staging measured faster for 1024-point y columns (-1..-15%), slower for 2048 (+1..2%)
     a.early = p->n1 == 1024;
     set_stage_waits(p, a);
@@ -254,6 +255,7 @@ ColArgs xpass_args(const fft3d_plan_s *p, CLayout src, CLayout dst, int inverse,
     a.early = pitch * (int64_t)p->csize >= ((int64_t)3 << 20);
     a.tiles_per_plane = 0;
     a.nyq_in_plane = 0;
+    a.pf_stride = 0;
     a.bulk = bulk_mode(p, src, 0, w);
     a.err = p->status;
     set_stage_waits(p, a);
@@ -285,6 +287,7 @@ int run_fused(fft3d_plan p, int kind, const ZArgs &z, CLayout ylayout, int forwa
     f.y.early = 0;
     f.y.stall_tx = 0;
     f.y.stage_polls = kStageWaitPolls;
+    f.y.pf_stride = 0;
     f.n0 = p->n0;
     f.zi = p->n1 / p->fz_lines;
 #ifndef FFT3D_FUSED_LAG

@@ -152,6 +152,7 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
         a.bulk = 0;
         a.err = err_flag;
         a.early = 0;
+        a.pf_stride = 0;
         a.stall_tx = 0;
         a.stage_polls = kStageWaitPolls;
         e = f32 ? col_launch_f32((int)n0, a, tiles, tw0, nullptr, nullptr, st) : col_launch_f64((int)n0, a, tiles, tw0, nullptr, nullptr, st);
@@ -172,6 +173,7 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
         a.bulk = 0;
         a.err = err_flag;
         a.early = 0;
+        a.pf_stride = 0;
         a.stall_tx = 0;
         a.stage_polls = kStageWaitPolls;
         a.tiles_per_field = 1;

@@ -56,6 +56,7 @@ struct ColArgs {
                               // (selects the kernel instance)
     unsigned stall_tx;        // pipelined pass, test hook: bytes a tile wait expects beyond its copies
     long long stage_polls;    // pipelined pass: polls of a tile wait before it gives up
+    int64_t pf_stride;        // one-tile pass: > 0 prefetch tile blockIdx + pf_stride into L2 (the next wave)
 };
 
 template <typename C>
@@ -163,7 +164,7 @@ template <typename C> __device__ __forceinline__ C load_cg(const C *p) { return 
 // loaded straight into registers.  CG selects L2-only loads.
 template <typename R, int L, int E, int W, bool CG, bool INV>
 __device__ __forceinline__ void col_tile(const ColArgs &a, int64_t tile, unsigned char *smem,
-                                         const typename cvec<R>::T *__restrict__ tw)
+                                         const typename cvec<R>::T *__restrict__ tw, int64_t pf_tile = -1)
 {
     typedef typename cvec<R>::T C;
     constexpr int NT = L / E;
@@ -180,6 +181,16 @@ __device__ __forceinline__ void col_tile(const ColArgs &a, int64_t tile, unsigne
     for (int i = 0; i < E; ++i) {
         v[i] = CG ? load_cg(sj + i * sstep) : sj[i * sstep];
         if (INV) v[i] = cswap(v[i]);
+    }
+    if (pf_tile >= 0) {
+        // the tile this SM is likely to run next: its rows into L2 while this one is transformed
+        C *psp = nullptr, *pdp = nullptr;
+        int64_t pss = 0, pds = 0;
+        col_decode<C, W>(a, pf_tile, c, psp, pss, pdp, pds);
+        const C *pj = psp + (int64_t)j * pss;
+        const int64_t pstep = (int64_t)NT * pss;
+#pragma unroll
+        for (int i = 0; i < E; ++i) asm volatile("prefetch.global.L2 [%0];\n" ::"l"(pj + i * pstep));
     }
     ColEx<C, W> ex{(C *)smem, c};
     line_fft<R, L, E>(v, j, tw, ex);
@@ -201,7 +212,8 @@ __global__ void __launch_bounds__(W *(L / E))
 colpass_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    col_tile<R, L, E, W, false, INV>(a, blockIdx.x, smem_raw, tw);
+    const int64_t pf = a.pf_stride > 0 && blockIdx.x + a.pf_stride < gridDim.x ? blockIdx.x + a.pf_stride : -1;
+    col_tile<R, L, E, W, false, INV>(a, blockIdx.x, smem_raw, tw, pf);
 }
 
 template <int L> __host__ __device__ constexpr int split_rows() { return L + (L >> 5) + 1; }
