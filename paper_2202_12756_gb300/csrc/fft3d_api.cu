@@ -398,6 +398,7 @@ int forward_pipeline(fft3d_plan p, const void *in, void *out, cudaStream_t st, d
     z.nlines = p->nb0 * p->n1;
     z.scale_edge = se;
     z.scale_mid = sm;
+    z.pf_lines = 0;
     z.max_blocks = (in != out && host_resident(in)) ? FFT3D_HOST_Z_BLOCKS : 0;
     int rc;
     if (p->fused) {
@@ -445,6 +446,7 @@ int inverse_pipeline(fft3d_plan p, const void *in, void *out, cudaStream_t st, d
     z.nlines = p->nb0 * p->n1;
     z.scale_edge = we;
     z.scale_mid = s;
+    z.pf_lines = 0;
     z.max_blocks = (!inplace && host_resident(out)) ? FFT3D_HOST_Z_BLOCKS : 0;
     if (p->fused) return run_fused(p, K_C2R_YZ, z, dst, 0, st);
     if (p->n1 > 1) {

@@ -189,6 +189,7 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
     z.nlines = n0 * n1;
     z.scale_edge = 1.0;
     z.scale_mid = 1.0 / ((double)n0 * (double)n1 * (double)n2);
+    z.pf_lines = 0;
     z.max_blocks = 0;
     e = f32 ? zc2r_launch_f32((int)m, z, twz, rot, st) : zc2r_launch_f64((int)m, z, twz, rot, st);
     return e == cudaSuccess ? FFT3D_OK : FFT3D_ERR_CUDA;

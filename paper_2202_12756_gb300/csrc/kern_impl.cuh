@@ -321,8 +321,12 @@ inline cudaError_t zr2c_launch_t(const ZArgs &a, const void *tw, const void *rot
     typedef const typename cvec<R>::T *TW;
     if (a.max_blocks > 0 && blocks > a.max_blocks)
         zpass_r2c_kernel<R, M, E, LPB, true><<<(unsigned)a.max_blocks, g.threads, g.smem, st>>>(a, (TW)tw, (TW)rot);
-    else
-        zpass_r2c_kernel<R, M, E, LPB, false><<<(unsigned)blocks, g.threads, g.smem, st>>>(a, (TW)tw, (TW)rot);
+    else {
+        auto k = zpass_r2c_kernel<R, M, E, LPB, false>;
+        ZArgs b = a;
+        b.pf_lines = z_l2pf<R, M>() ? (int64_t)persistent_grid(k, g.threads, g.smem, (int64_t)1 << 40) * LPB : 0;
+        k<<<(unsigned)blocks, g.threads, g.smem, st>>>(b, (TW)tw, (TW)rot);
+    }
     return cudaGetLastError();
 }
 
@@ -336,8 +340,12 @@ inline cudaError_t zc2r_launch_t(const ZArgs &a, const void *tw, const void *rot
     typedef const typename cvec<R>::T *TW;
     if (a.max_blocks > 0 && blocks > a.max_blocks)
         zpass_c2r_kernel<R, M, E, LPB, true><<<(unsigned)a.max_blocks, g.threads, g.smem, st>>>(a, (TW)tw, (TW)rot);
-    else
-        zpass_c2r_kernel<R, M, E, LPB, false><<<(unsigned)blocks, g.threads, g.smem, st>>>(a, (TW)tw, (TW)rot);
+    else {
+        auto k = zpass_c2r_kernel<R, M, E, LPB, false>;
+        ZArgs b = a;
+        b.pf_lines = z_l2pf<R, M>() ? (int64_t)persistent_grid(k, g.threads, g.smem, (int64_t)1 << 40) * LPB : 0;
+        k<<<(unsigned)blocks, g.threads, g.smem, st>>>(b, (TW)tw, (TW)rot);
+    }
     return cudaGetLastError();
 }
 
