@@ -324,7 +324,7 @@ inline cudaError_t zr2c_launch_t(const ZArgs &a, const void *tw, const void *rot
     else {
         auto k = zpass_r2c_kernel<R, M, E, LPB, false>;
         ZArgs b = a;
-        b.pf_lines = z_l2pf<R, M>() ? (int64_t)persistent_grid(k, g.threads, g.smem, (int64_t)1 << 40) * LPB : 0;
+        b.pf_lines = z_l2pf<R, M, false>() ? (int64_t)persistent_grid(k, g.threads, g.smem, (int64_t)1 << 40) * LPB : 0;
         k<<<(unsigned)blocks, g.threads, g.smem, st>>>(b, (TW)tw, (TW)rot);
     }
     return cudaGetLastError();
@@ -343,7 +343,7 @@ inline cudaError_t zc2r_launch_t(const ZArgs &a, const void *tw, const void *rot
     else {
         auto k = zpass_c2r_kernel<R, M, E, LPB, false>;
         ZArgs b = a;
-        b.pf_lines = z_l2pf<R, M>() ? (int64_t)persistent_grid(k, g.threads, g.smem, (int64_t)1 << 40) * LPB : 0;
+        b.pf_lines = z_l2pf<R, M, true>() ? (int64_t)persistent_grid(k, g.threads, g.smem, (int64_t)1 << 40) * LPB : 0;
         k<<<(unsigned)blocks, g.threads, g.smem, st>>>(b, (TW)tw, (TW)rot);
     }
     return cudaGetLastError();

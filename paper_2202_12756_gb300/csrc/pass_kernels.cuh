@@ -850,10 +850,14 @@ template <int M, int E> __host__ __device__ constexpr int zline_smem_elems()
 
 // z-pass kernels (one line group per block) that prefetch into L2, right
 // after their own loads, the input lines one wave of resident blocks ahead:
-// float lines of 512 points.  Measured on GB300 at 1024^3: both z-passes
-// 1.29 -> 1.21 ms (7.1 TB/s); at M = 1024 1-2% slower, and at M = 768 the
-// prefetch code raises the kernels' registers, so those lengths do without.
-template <typename R, int M> __host__ __device__ constexpr bool z_l2pf() { return sizeof(R) == 4 && M == 512; }
+// float lines of 512 points, and the C2R kernel of 768-point lines.
+// Measured on GB300: at 1024^3 both z-passes 1.29 -> 1.21 ms (7.1 TB/s); at
+// 1536^3 the C2R pass 6.1 -> 5.2 ms; at M = 1024 1-2% slower, and in the
+// 768-point R2C kernel the prefetch code raises the registers (120 -> 156).
+template <typename R, int M, bool C2R> __host__ __device__ constexpr bool z_l2pf()
+{
+    return sizeof(R) == 4 && (M == 512 || (C2R && M == 768));
+}
 
 #ifndef FFT3D_ROTCONST
 #define FFT3D_ROTCONST 1
@@ -1079,7 +1083,7 @@ zpass_r2c_kernel(ZArgs a, const typename cvec<R>::T *__restrict__ tw,
             zr2c_lines<R, M, E, LPB>(a, blk * LPB, smem_raw, tw, rot);
         }
     } else {
-        zr2c_lines<R, M, E, LPB, z_l2pf<R, M>()>(a, (int64_t)blockIdx.x * LPB, smem_raw, tw, rot);
+        zr2c_lines<R, M, E, LPB, z_l2pf<R, M, false>()>(a, (int64_t)blockIdx.x * LPB, smem_raw, tw, rot);
     }
 }
 
@@ -1095,7 +1099,7 @@ zpass_c2r_kernel(ZArgs a, const typename cvec<R>::T *__restrict__ tw,
             zc2r_lines<R, M, E, LPB, false>(a, blk * LPB, smem_raw, tw, rot);
         }
     } else {
-        zc2r_lines<R, M, E, LPB, false, z_l2pf<R, M>()>(a, (int64_t)blockIdx.x * LPB, smem_raw, tw, rot);
+        zc2r_lines<R, M, E, LPB, false, z_l2pf<R, M, true>()>(a, (int64_t)blockIdx.x * LPB, smem_raw, tw, rot);
     }
 }
 
