@@ -227,8 +227,11 @@ ColArgs ypass_args(const fft3d_plan_s *p, CLayout src, CLayout dst, int inverse,
     a.err = p->status;
     a.tiles_per_field = 1;
     a.pf_stride = 0;
-    // early staging measured faster for 1024-point y columns (-1..-15%), slower for 2048 (+1..2%)
-    a.early = p->n1 == 1024;
+    a.tickets = p->status + 1;
+    // the next tile is staged after the first exchange barrier, not right after the registers
+    // are loaded: measured on GB300 with the dynamic tile order, 1024-point y columns are 1-2%
+    // faster that way (with the static order early staging was 1-15% faster for them)
+    a.early = 0;
     set_stage_waits(p, a);
     *tiles = a.tiles_main + (p->nb0 + w - 1) / w;
     return a;
@@ -258,6 +261,7 @@ ColArgs xpass_args(const fft3d_plan_s *p, CLayout src, CLayout dst, int inverse,
     a.pf_stride = 0;
     a.bulk = bulk_mode(p, src, 0, w);
     a.err = p->status;
+    a.tickets = p->status + 1;
     set_stage_waits(p, a);
     return a;
 }
@@ -288,6 +292,7 @@ int run_fused(fft3d_plan p, int kind, const ZArgs &z, CLayout ylayout, int forwa
     f.y.stall_tx = 0;
     f.y.stage_polls = kStageWaitPolls;
     f.y.pf_stride = 0;
+    f.y.tickets = nullptr;
     f.n0 = p->n0;
     f.zi = p->n1 / p->fz_lines;
 #ifndef FFT3D_FUSED_LAG
@@ -326,6 +331,12 @@ int run_colpass(fft3d_plan p, int kind, ColArgs a, int64_t tiles, int L, const v
     if (!ok) a.bulk = 0;
     if (a.bulk) mp = &map;
     if (a.bulk == 2) mp2 = &map2;
+    const PassGeom &g = a.axis == 0 ? p->g0 : p->g1;
+    if (!g.persistent || g.pair) a.tickets = nullptr;  // only the pipelined kernel draws tiles
+    if (a.tickets) {
+        const cudaError_t e = cudaMemsetAsync(a.tickets, 0, sizeof(unsigned), st);
+        if (e != cudaSuccess) return set_err(p, FFT3D_ERR_CUDA, "cudaMemsetAsync", e);
+    }
     return run_pass(p, kind, st, [&] { return col_launch(p, L, a, tiles, tw, st, mp, mp2); });
 }
 

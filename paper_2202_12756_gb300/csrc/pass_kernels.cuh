@@ -57,6 +57,7 @@ struct ColArgs {
     unsigned stall_tx;        // pipelined pass, test hook: bytes a tile wait expects beyond its copies
     long long stage_polls;    // pipelined pass: polls of a tile wait before it gives up
     int64_t pf_stride;        // one-tile pass: > 0 prefetch tile blockIdx + pf_stride into L2 (the next wave)
+    unsigned *tickets;        // pipelined pass: zeroed tile counter (dynamic tile order), or null (static order)
 };
 
 template <typename C>
@@ -284,11 +285,12 @@ template <typename C, int W, int L> __host__ __device__ constexpr int stage_elem
 constexpr long long kStageWaitPolls = 1LL << 22;
 
 // Shared memory of the pipelined column pass: staging (L/2 W + L/2 (W + 2)
-// complex), the split exchange buffer, the mbarrier, then the twiddle table.
+// complex), the split exchange buffer, the mbarrier and two tile slots (32
+// bytes), then the twiddle table.
 template <typename R, int L, int E, int W> __host__ __device__ constexpr size_t pipe_smem_bytes()
 {
     return (size_t)stage_elems<typename cvec<R>::T, W, L>() * sizeof(typename cvec<R>::T) +
-           (size_t)split_rows<L>() * W * sizeof(R) + 16 + (size_t)line_tw_size(L, E) * sizeof(typename cvec<R>::T);
+           (size_t)split_rows<L>() * W * sizeof(R) + 32 + (size_t)line_tw_size(L, E) * sizeof(typename cvec<R>::T);
 }
 
 // Persistent, software-pipelined column pass.  Each block walks the tiles
@@ -336,7 +338,8 @@ colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
     C *stage_odd = stage + L / 2 * W;  // mode 2: odd rows, W + 2 wide
     R *exbuf = (R *)(stage + stage_elems<C, W, L>());
     uint64_t *mbar = (uint64_t *)(exbuf + split_rows<L>() * W);
-    C *tws = (C *)(mbar + 2);  // the block's copy of the twiddle table
+    int64_t *tslot = (int64_t *)(mbar + 2);  // dynamic order: tiles drawn one iteration ahead
+    C *tws = (C *)(mbar + 4);                // the block's copy of the twiddle table
     constexpr int NTW = line_tw_size(L, E);
     for (int i = threadIdx.x; i < NTW; i += blockDim.x) tws[i] = __ldg(tw + i);
     const int c = threadIdx.x % W;
@@ -399,21 +402,26 @@ colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
         return mode;
     };
 
-    // Tiles t = blockIdx.x + q gridDim.x: at any moment the blocks work on
-    // neighbouring tiles, whose rows share DRAM pages (measured on GB300:
-    // giving each block runs of 2, 4 or 8 consecutive tiles instead slows
-    // the y-pass by 15, 27 and 45%).
+    // Tile order.  Static: t = blockIdx.x + q gridDim.x, so that at any moment
+    // the blocks work on neighbouring tiles, whose rows share DRAM pages
+    // (measured on GB300: giving each block runs of 2, 4 or 8 consecutive
+    // tiles instead slows the y-pass by 15, 27 and 45%, and runs of 2 to all
+    // of a block's tiles gain nothing in the x-pass).  Dynamic (a.tickets):
+    // a block's first two tiles are blockIdx.x and blockIdx.x + gridDim.x,
+    // and each later one is 2 gridDim.x + a ticket drawn from *a.tickets
+    // (zeroed before the launch), one iteration ahead so that the atomic's
+    // latency stays off the tile's path: slots tslot[q & 1] alternate, each
+    // written after one staging barrier and read after the next.  Tickets go
+    // out in time order, so a block whose next tile is past the end has no
+    // later tile pending.  Blocks that run faster take more tiles, and the
+    // pass no longer waits for the slowest SM's share.
+    const bool dyn = a.tickets != nullptr;
     int64_t t = blockIdx.x;
     C *sp = nullptr, *dp = nullptr;
     int64_t ss = 0, ds = 0;
     bool valid = t < ntiles && col_decode<C, W>(a, t, c, sp, ss, dp, ds);
     int mode = t < ntiles ? fill(t, sp, ss) : 0;
-    while (t < ntiles) {
-        const int64_t tn = t + gridDim.x;
-        C *spn = nullptr, *dpn = nullptr;
-        int64_t ssn = 0, dsn = 0;
-        const bool validn = tn < ntiles && col_decode<C, W>(a, tn, c, spn, ssn, dpn, dsn);
-
+    for (int q = 0; t < ntiles; ++q) {
         if (mode) {
             const bool ok = mbar_wait_bounded(mb, phase, a.stage_polls);
             if (__syncthreads_or(!ok)) {
@@ -424,7 +432,13 @@ colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
             phase ^= 1u;
         } else {
             cp_async_wait_all();  // this thread's copies of tile t have landed
+            if (dyn) __syncthreads();  // orders the tile slots (written after the previous barrier)
         }
+        const int64_t tn = (dyn && q > 0) ? tslot[(q - 1) & 1] : t + gridDim.x;
+        if (dyn && threadIdx.x == 0) tslot[q & 1] = 2 * (int64_t)gridDim.x + atomicAdd(a.tickets, 1u);
+        C *spn = nullptr, *dpn = nullptr;
+        int64_t ssn = 0, dsn = 0;
+        const bool validn = tn < ntiles && col_decode<C, W>(a, tn, c, spn, ssn, dpn, dsn);
         C v[E];
         if (mode == 2) {
             // rows j + i NT (NT even) share the parity of j
