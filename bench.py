@@ -7,7 +7,11 @@ generated in FP64).  The same pair in FP64 is timed too and reported under
 modes, amplitude |k|^(-11/6) for 1 <= |k| <= 512, seed 2) taken to real space
 by the library's own FP64 inverse, normalised to unit RMS and rounded once to
 FP32.  The arrays (4.3 GB FP32, 8.6 GB FP64) are far larger than the 129 MB
-L2, so no L2 flush is needed between steps.
+L2, so no L2 flush is needed between steps.  The headline is timed with the
+library's per-pass profiling off; per-pass times come from a second, profiled
+run of the same pairs right after it.  On one GPU the other grids of the
+paper's runs (512^3 FP64, 1536^3 and 2048^3 FP32, 2048^3 FP64; Sec. 4, Tables
+3-4) are timed as well, under "configs".
 
 metric: GFLOP/s with 2.5 N^3 log2(N^3) flops per real transform (5 per pair
 element-log), i.e. 5 N^3 log2(N^3) per pair; also HBM GB/s of the three
@@ -63,6 +67,45 @@ def measured_peaks():
         d = json.load(open(p))
         return {"hbm_gbs": d.get("hbm_gbs"), "src": "measured"}
     return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+def fp64_op_counts(workload):
+    """FP64 instructions per complex half-spectrum element of each pass
+    (dadd, dmul, dfma; counted by ncu on a small case of the same line
+    lengths), or None when the kernels changed since they were counted."""
+    p = os.path.join(ROOT, "profiles", "fp64_ops.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_hash") != kernel_sources_hash():
+        return None
+    return d.get("workloads", {}).get(workload)
+
+
+def fp64_roofline(stats, ops, peak, units):
+    """FP64-ALU roofline of the slowest FP64 pass: its FP64 instructions per
+    launch (ops per element x units) over its mean launch time, against the
+    measured FP64 instruction rate (the best of FMA, add and multiply; each
+    takes one FP64 issue slot)."""
+    if not stats or not peak:
+        return None
+    top = max(stats, key=lambda s: s["total_ms"])
+    avg_ms = top["total_ms"] / top["launches"]
+    peak_inst = max(peak["fma_gflops"] / 2.0, peak["add_gflops"], peak["mul_gflops"])
+    r = {"bound": "fp64_alu", "kernel": top["name"], "avg_launch_ms": round(avg_ms, 4),
+         "peak": round(peak_inst, 1), "unit": "G FP64 instructions/s",
+         "peak_measured_gflops": {k: round(v, 1) for k, v in peak.items()}}
+    c = (ops or {}).get(top["name"])
+    if c is None:
+        r.update({"achieved": None, "frac": None, "ops_per_element": None})
+        return r
+    per_el = c["dadd"] + c["dmul"] + c["dfma"]
+    achieved = per_el * units / (avg_ms * 1e-3) / 1e9
+    flops = (c["dadd"] + c["dmul"] + 2 * c["dfma"]) * units / (avg_ms * 1e-3) / 1e9
+    r.update({"achieved": round(achieved, 1), "frac": round(achieved / peak_inst, 4),
+              "ops_per_element": c, "achieved_gflops": round(flops, 1),
+              "flops_frac_of_fma_peak": round(flops / peak["fma_gflops"], 4)})
+    return r
 
 
 def ncu_traffic(workload):
@@ -178,6 +221,9 @@ def make_field(grid, dev):
 
 
 def time_pairs(plan, buf, steps, warmup, dev, pg, profile=False):
+    """ms over `steps` in-place pairs on the current stream (after `warmup`
+    untimed ones), the plan's launches in them, per-pass stats when
+    `profile`, and the sorted per-step times."""
     import torch
     stream = torch.cuda.current_stream(dev)
     for _ in range(warmup):
@@ -206,6 +252,10 @@ def time_pairs(plan, buf, steps, warmup, dev, pg, profile=False):
     return ms, launches, stats, per_step
 
 
+def per_pass(stats, nd=4):
+    return {s["name"]: round(s["total_ms"] / s["launches"], nd) for s in stats}
+
+
 def roofline_from(stats, peak_gbs, traffic):
     if not stats:
         return None
@@ -216,7 +266,7 @@ def roofline_from(stats, peak_gbs, traffic):
             "unit": "GB/s", "frac": round(achieved / peak_gbs, 4),
             "traffic": (traffic or {}).get(top["name"]),
             "avg_launch_ms": round(avg_ms, 4),
-            "per_pass_ms": {s["name"]: round(s["total_ms"] / s["launches"], 4) for s in stats}}
+            "per_pass_ms": per_pass(stats)}
 
 
 def cpu_baseline(budget_s=12.0, n=256):
@@ -282,6 +332,14 @@ def workload_config(grid, world):
             "l2": f"inputs ({n0 * n1 * (n // 2 + 1) * 8 / 1e9:.2f} GB) larger than L2, no flush"}
 
 
+def reference_config(n, world):
+    """The `config` of the reference arm: what it actually times."""
+    return {"workload": f"{n}x{n}x{n} real grid, FP64 R2C+C2R pair out of place, the CPU oracle "
+                        f"(plain mixed-radix FFT, OpenMP over lines) on the host cores, uniform field (seed 0)",
+            "grid": [n, n, n], "dtype": "f64", "layout": "out-of-place dense", "device": "host cores",
+            "parallelism": f"rank 0 of {world}"}
+
+
 def bench_grid(args):
     return tuple(int(x) for x in args.grid.split(",")) if args.grid else (args.n,) * 3
 
@@ -305,7 +363,7 @@ def run_reference(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(bench_grid(args), world),
+            "config": reference_config(n, world),
             "cpu_baseline": {"value": round(val, 3), "unit": UNIT, "cores": oracle.num_threads(),
                              "kind": "oracle",
                              "sample": f"each step one FP64 R2C+C2R pair of a {n}^3 uniform field (the oracle "
@@ -313,6 +371,47 @@ def run_reference(args):
             "e2e": {"value": round(val, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# The paper's other grids (Sec. 4, Tables 3-4), timed on one GPU beside the
+# headline: (grid, dtype, warm-up pairs, timed pairs).  Each runs in place on a
+# device-drawn uniform field; its round-trip error is sampled on four planes.
+OTHER_CONFIGS = [((512, 512, 512), "f64", 3, 10), ((1536, 1536, 1536), "f32", 3, 10),
+                 ((2048, 2048, 2048), "f32", 3, 5), ((2048, 2048, 2048), "f64", 1, 2)]
+
+
+def other_configs(dev, peak_gbs):
+    import torch
+    import paper_2202_12756_gb300 as fft3d
+    out = []
+    for grid, name, warm, steps in OTHER_CONFIGS:
+        n0, n1, n2 = grid
+        dt = torch.float32 if name == "f32" else torch.float64
+        plan = fft3d.Plan(grid, dt, dev)
+        buf = plan.empty_padded()
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(7)
+        buf.uniform_(-1.0, 1.0, generator=gen)
+        planes = [0, n0 // 3, 2 * n0 // 3, n0 - 1]
+        x0 = buf[planes, :, :n2].clone()
+        plan.r2c_(buf)
+        plan.c2r_(buf)
+        rt = float((buf[planes, :, :n2] - x0).double().norm() / x0.double().norm())
+        del x0
+        ms, _, _, _ = time_pairs(plan, buf, steps, warm, dev, None)
+        _, _, stats, _ = time_pairs(plan, buf, 1, 0, dev, None, profile=True)
+        t = ms / steps
+        rsize = 4 if name == "f32" else 8
+        gbs = 2 * pass_bytes(n0, n1, n2, rsize) / (t * 1e-3) / 1e9
+        out.append({"grid": list(grid), "dtype": name, "layout": "in-place padded", "pairs_timed": steps,
+                    "ms_per_pair": round(t, 3), "gflops": round(pair_flops(n0, n1, n2) / (t * 1e-3) / 1e9, 1),
+                    "pass_gbs": round(gbs, 1), "hbm_frac_of_peak": round(gbs / peak_gbs, 4),
+                    "per_pass_ms": per_pass(stats, 3), "round_trip_rel_l2_sampled": rt,
+                    "field": "uniform[-1,1) drawn on the device (torch generator, seed 7); round trip on planes "
+                             + ",".join(map(str, planes))})
+        del buf, plan
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_ours(args):
@@ -334,26 +433,32 @@ def run_ours(args):
     buf32 = plan32.empty_padded()
     buf32.copy_(buf64)
 
-    # ---- FP32 headline: device-resident inputs
+    # ---- FP32 headline: device-resident inputs, profiling off
     clocks = ClockSampler(local)
     clocks.start()
-    ms32, launches32, stats32, steps32 = time_pairs(plan32, buf32, args.steps, args.warmup, dev, pg, profile=True)
+    ms32, launches32, _, steps32 = time_pairs(plan32, buf32, args.steps, args.warmup, dev, pg)
     clk = clocks.stop()
     ms32 = max_over_ranks(ms32, pg, dev)
     t_step = ms32 / args.steps
     flops = pair_flops(n0, n1, n)
     bytes_pair = 2 * pass_bytes(n0, n1, n, 4)
     value = flops * world / (t_step * 1e-3) / 1e9
+    # per-pass CUDA events (on the plan's stream) from a second run of the same pairs
+    prof_steps = max(5, args.steps // 4)
+    ms32p, _, stats32, _ = time_pairs(plan32, buf32, prof_steps, 1, dev, pg, profile=True)
 
     # ---- reference point: cuFFT through torch.fft on the same field (rank 0)
     torch_ref = torch_fft_reference(buf32, grid, dev) if rank == 0 else None
 
-    # ---- FP64 pair (same field)
+    # ---- FP64 pair (same field), then its per-pass times and the FP64 roof
     steps64 = max(2, args.steps // 10)
-    ms64, launches64, stats64, _ = time_pairs(plan64, buf64, steps64, args.warmup, dev, pg, profile=True)
+    ms64, launches64, _, _ = time_pairs(plan64, buf64, steps64, args.warmup, dev, pg)
     ms64 = max_over_ranks(ms64, pg, dev)
     t64 = ms64 / steps64
+    _, _, stats64, _ = time_pairs(plan64, buf64, 2, 0, dev, pg, profile=True)
     del buf64
+    fp64_peak = fft3d.fft3d_measure_fp64_peak()
+    units = n0 * n1 * (n // 2 + 1)  # complex half-spectrum elements per pass launch
 
     # ---- end to end through the public API with the field in pinned host
     # memory: the forward's first pass reads it straight from host memory and
@@ -420,10 +525,13 @@ def run_ours(args):
         "hbm_frac_of_peak": round(bytes_pair / (t_step * 1e-3) / 1e9 / peak, 4),
         "gflops_paper_convention": round(2 * value, 1),
         "roofline": roofline_from(stats32, peak, traffic),
+        "per_pass_timing": f"CUDA events around each pass on the plan's stream, {prof_steps} profiled pairs "
+                           f"right after the timed region ({ms32p / prof_steps:.4f} ms per pair with the events)",
         "fp64": {"ms_per_step": round(t64, 3),
                  "gflops": round(flops * world / (t64 * 1e-3) / 1e9, 1),
                  "hbm_gbs": round(2 * pass_bytes(n0, n1, n, 8) / (t64 * 1e-3) / 1e9, 1),
-                 "per_pass_ms": {s["name"]: round(s["total_ms"] / s["launches"], 3) for s in stats64},
+                 "per_pass_ms": per_pass(stats64, 3),
+                 "roofline": fp64_roofline(stats64, fp64_op_counts(f"{n0}x{n1}x{n} f64"), fp64_peak, units),
                  "fp32_speedup": round(t64 / t_step, 2)},
         "e2e": {"value": round(e2e_val, 1), "unit": UNIT, "ms_per_step": round(ms_e2e, 3),
                 "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
@@ -441,6 +549,11 @@ def run_ours(args):
         line["torch_fft_reference"] = torch_ref
     rt = round_trip_error(plan32, host_in, host_out)
     line["fp32_round_trip_rel_l2"] = rt
+    del host_in, host_out
+    if world == 1 and not args.no_configs:
+        del plan64, plan32
+        torch.cuda.empty_cache()
+        line["configs"] = other_configs(dev, peak)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -461,6 +574,8 @@ def main():
                     help="N0,N1,N2 instead of N^3 (profiling and smaller cases)")
     ap.add_argument("--ref-n", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other grids (512^3 FP64, 1536^3 / 2048^3 FP32, 2048^3 FP64)")
     ap.add_argument("--fused", action="store_true",
                     help="run the FP32 plans with the opt-in fused plane pass (profiling)")
     args = ap.parse_args()

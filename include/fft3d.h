@@ -248,18 +248,47 @@ int fft3d_plan_info(fft3d_plan plan, int *fused_plane_pass);
  *     exits;
  *   - all calls share it and it keeps the last call's contents; calls that
  *     overlap on the GPU (other streams, other host threads) race on it;
- *   - nothing in it needs clearing: each call rewrites the tables, and the
- *     scratch plane is written in full before it is read;
+ *   - nothing in it needs clearing by the caller: each call rewrites the
+ *     tables, writes the scratch plane in full before reading it, and clears
+ *     the device error word (below) on `stream` before its kernels run;
  *   - the first call on a device performs set-up (cudaGetSymbolAddress of
  *     the array and the kernels' shared-memory limits); make that first call
- *     before any stream capture.
- * Sizes beyond the array, n0 * n1 * (8 bytes for FFT3D_F32, 16 for
- * FFT3D_F64) > FFT3D_NOALLOC_SCRATCH_BYTES, are rejected with FFT3D_ERR_SIZE
- * before any work is queued, as are unsupported lengths.
+ *     before any stream capture.  The set-up belongs to the device's current
+ *     CUDA context: after a device reset the next call repeats it.
+ * Out of place, sizes beyond the array's scratch plane, n0 * n1 * (8 bytes
+ * for FFT3D_F32, 16 for FFT3D_F64) > FFT3D_NOALLOC_SCRATCH_BYTES, are
+ * rejected with FFT3D_ERR_SIZE before any work is queued (in place,
+ * in_cplx == out_real, needs no scratch plane and has no such limit), as are
+ * unsupported lengths.
+ * The 2048-point x-pass (n0 = 2048, FFT3D_F32) runs each tile on a cluster of
+ * two blocks whose waits for each other are bounded; a wait that runs out
+ * leaves the output invalid and sets the array's device error word, which
+ * this call cannot report (it returns before its kernels run): read it with
+ * fft3d_noalloc_status.
  */
 #define FFT3D_NOALLOC_SCRATCH_BYTES (8u << 20)
 int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64_t n0, int64_t n1, int64_t n2,
                            int dtype, void *stream);
+
+/*
+ * Device error word of fft3d_exec_c2r_noalloc on the current device: 1 if a
+ * bounded wait in one of its calls ran out since the word was last cleared
+ * (by a call, or by this function), else 0.  Synchronises the device, stores
+ * the word in *device_error and clears it.  Allocates nothing.  The paper
+ * has no counterpart.
+ */
+int fft3d_noalloc_status(int *device_error);
+
+/*
+ * FP64 throughput of the current device, measured: the roof of the FP64
+ * passes, which on GB300 are bound by FP64 add / multiply issue rather than
+ * by HBM (the paper compares single and double precision in Sec. 4, Table
+ * 3).  Runs three short kernels (FMA, add and multiply chains that fill every
+ * SM) on a private stream and synchronises; stores the best of three timed
+ * launches of each in GFLOP/s (an FMA counts two flops, an add or multiply
+ * one).  A diagnostic for the bench; it touches no plan or user memory.
+ */
+int fft3d_measure_fp64_peak(double *fma_gflops, double *add_gflops, double *mul_gflops);
 
 #ifdef __cplusplus
 }

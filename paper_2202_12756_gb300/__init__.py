@@ -46,7 +46,8 @@ EXPORTED = (
     "fft3d_plan_last_error", "fft3d_supported_length", "fft3d_plan_set_profiling",
     "fft3d_plan_profile_read", "fft3d_plan_launch_count", "fft3d_exec_c2r_noalloc",
     "fft3d_plan_status", "fft3d_plan_set_debug", "fft3d_plan_info", "fft3d_plan_set_fused",
-    "fft3d_exec_c2r_overwrite", "fft3d_plan_create_batched",
+    "fft3d_exec_c2r_overwrite", "fft3d_plan_create_batched", "fft3d_noalloc_status",
+    "fft3d_measure_fp64_peak",
 )
 
 
@@ -91,6 +92,9 @@ def _declare(lib):
     lib.fft3d_plan_set_debug.argtypes = [P, ctypes.c_int, I64]
     lib.fft3d_plan_info.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
     lib.fft3d_plan_set_fused.argtypes = [P, ctypes.c_int]
+    lib.fft3d_noalloc_status.argtypes = [ctypes.POINTER(ctypes.c_int)]
+    D = ctypes.POINTER(ctypes.c_double)
+    lib.fft3d_measure_fp64_peak.argtypes = [D, D, D]
     return lib
 
 
@@ -230,6 +234,23 @@ def fft3d_exec_c2r_noalloc(in_cplx, out_real, n0, n1, n2, dtype, stream):
     call cudaMalloc); see include/fft3d.h for the shared-scratch rules."""
     _check(load_library().fft3d_exec_c2r_noalloc(in_cplx, out_real, n0, n1, n2, dtype, stream),
            "fft3d_exec_c2r_noalloc")
+
+
+def fft3d_noalloc_status():
+    """Device error word (0/1) of fft3d_exec_c2r_noalloc on the current
+    device; synchronises the device and clears it."""
+    v = ctypes.c_int()
+    _check(load_library().fft3d_noalloc_status(ctypes.byref(v)), "fft3d_noalloc_status")
+    return v.value
+
+
+def fft3d_measure_fp64_peak():
+    """Measured FP64 GFLOP/s of the current device for FMA (2 flops each),
+    add and multiply chains (see include/fft3d.h)."""
+    f, a, m = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load_library().fft3d_measure_fp64_peak(ctypes.byref(f), ctypes.byref(a), ctypes.byref(m)),
+           "fft3d_measure_fp64_peak")
+    return {"fma_gflops": f.value, "add_gflops": a.value, "mul_gflops": m.value}
 
 
 # ------------------------------------------------------------ torch layer
@@ -407,11 +428,16 @@ _plans_lock = threading.Lock()
 
 
 def get_plan(shape, dtype, device, batch=1):
+    """The cached plan for (shape, dtype, device, batch) on the device's
+    current torch stream.  A plan serves one stream at a time (its scratch
+    plane and tile counter are shared by its calls), so each stream gets a
+    plan of its own."""
     torch = _torch()
     device = torch.device(device)
     if device.index is None:
         device = torch.device("cuda", torch.cuda.current_device())
-    key = (tuple(int(s) for s in shape), dtype, device.index, int(batch))
+    stream = torch.cuda.current_stream(device).cuda_stream
+    key = (tuple(int(s) for s in shape), dtype, device.index, int(batch), stream)
     with _plans_lock:
         p = _plans.get(key)
         if p is None:
@@ -433,29 +459,28 @@ def _split_batch(shape):
 def _make_autograd():
     torch = _torch()
 
+    # each pass looks its plan up on the stream it runs on (the backward may run on another)
     class RFFT3(torch.autograd.Function):
         @staticmethod
         def forward(ctx, x):
             b, shape = _split_batch(x.shape)
-            plan = get_plan(shape, x.dtype, x.device, b)
-            ctx.plan = plan
-            return plan.r2c(x.contiguous())
+            ctx.key = (shape, x.dtype, x.device, b)
+            return get_plan(*ctx.key).r2c(x.contiguous())
 
         @staticmethod
         def backward(ctx, G):
-            return ctx.plan.r2c_adjoint(G.contiguous())
+            return get_plan(*ctx.key).r2c_adjoint(G.contiguous())
 
     class IRFFT3(torch.autograd.Function):
         @staticmethod
         def forward(ctx, X, shape):
             b, shape = _split_batch(shape)
-            plan = get_plan(shape, real_of(X.dtype), X.device, b)
-            ctx.plan = plan
-            return plan.c2r(X.contiguous())
+            ctx.key = (shape, real_of(X.dtype), X.device, b)
+            return get_plan(*ctx.key).c2r(X.contiguous())
 
         @staticmethod
         def backward(ctx, g):
-            return ctx.plan.c2r_adjoint(g.contiguous()), None
+            return get_plan(*ctx.key).c2r_adjoint(g.contiguous()), None
 
     return RFFT3, IRFFT3
 

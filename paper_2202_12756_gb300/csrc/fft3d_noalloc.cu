@@ -21,12 +21,18 @@
 //    loads the library holds it until the process exits.
 //  * All calls share it.  Calls that overlap on the GPU (two streams, or two
 //    host threads) race on it and corrupt each other's results.
-//  * Nothing in it has to start at zero: every call rewrites the tables, and
-//    the x-pass writes the whole scratch plane before the y-pass reads it.
+//  * Nothing in it has to start at zero: every call rewrites the tables, the
+//    x-pass writes the whole scratch plane before the y-pass reads it, and
+//    the call clears the device error word (below) on its stream first.
 //  * The first call on a device does the set-up: it fetches the array's
 //    device address with cudaGetSymbolAddress and raises the shared-memory
 //    limit of every pass kernel.  Make that first call before any stream
-//    capture.
+//    capture.  The set-up belongs to the device's CUDA context: after a
+//    device reset (a new primary context) the next call repeats it.
+//  * The 2048-point x-pass runs each tile on a cluster of two blocks whose
+//    waits for each other are bounded; a wait that runs out sets the error
+//    word in the array, and fft3d_noalloc_status reads and clears it.
+#include <cuda.h>  // CUcontext (type only; cuCtxGetCurrent comes from the driver at run time)
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -48,7 +54,28 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kTableBytes + k
 
 constexpr int kMaxDevices = 128;
 std::mutex g_setup_mu;
-void *g_scratch_ptr[kMaxDevices];  // device address of g_noalloc_scratch, per device
+void *g_scratch_ptr[kMaxDevices];      // device address of g_noalloc_scratch, per device
+CUcontext g_scratch_ctx[kMaxDevices];  // the context that address and the kernel set-up belong to
+
+// Offset of the device error word: the table slack after the last twiddle
+// table (no table uses its final 256 bytes).
+constexpr size_t kErrOffset = kTableBytes - 256;
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+
+CtxGetCurrentFn ctx_get_current_fn()
+{
+    static CtxGetCurrentFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuCtxGetCurrent", &ptr, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (CtxGetCurrentFn)ptr;
+    });
+    return fn;
+}
 
 #define FFT3D_NA_PREP(L)                                                   \
     if ((e = col_prepare_f32(L)) != cudaSuccess) return e;                 \
@@ -66,21 +93,28 @@ cudaError_t prepare_all_kernels()
 }
 
 // Device address of the scratch array on the current device; the first call
-// per device looks it up and prepares the kernels.
+// per device (and per context of that device) looks it up and prepares the
+// kernels.
 cudaError_t scratch_for_current_device(void **out)
 {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    CtxGetCurrentFn get_ctx = ctx_get_current_fn();
+    if (!get_ctx) return cudaErrorUnknown;
+    CUcontext ctx = nullptr;  // null while no context is current in this thread yet
+    if (get_ctx(&ctx) != CUDA_SUCCESS) return cudaErrorUnknown;
     std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch_ptr[dev]) {
+    if (!ctx || !g_scratch_ptr[dev] || g_scratch_ctx[dev] != ctx) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // also makes the device's context current
         if (e != cudaSuccess) return e;
         e = prepare_all_kernels();
         if (e != cudaSuccess) return e;
+        if (get_ctx(&ctx) != CUDA_SUCCESS) return cudaErrorUnknown;
         g_scratch_ptr[dev] = p;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_ptr[dev];
     return cudaSuccess;
@@ -96,8 +130,9 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
         return FFT3D_ERR_SIZE;
     const bool f32 = dtype == FFT3D_F32;
     const size_t csize = f32 ? 8 : 16;
-    if ((size_t)n0 * (size_t)n1 * csize > kPlaneBytes) return FFT3D_ERR_SIZE;  // beyond the scratch plane
     if (!in_cplx || !out_real) return FFT3D_ERR_NULL;
+    // only an out-of-place call uses the scratch plane (in place, the output buffer holds every column)
+    if (in_cplx != out_real && (size_t)n0 * (size_t)n1 * csize > kPlaneBytes) return FFT3D_ERR_SIZE;
     if ((uintptr_t)in_cplx % csize || (uintptr_t)out_real % csize) return FFT3D_ERR_ALIGN;
     const int64_t m = n2 / 2, m1 = m + 1;
     if (in_cplx != out_real) {
@@ -120,12 +155,11 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
     char *twz = tw1 + kTableSlot;
     char *rot = twz + kTableSlot;
     void *plane = (char *)scratch + kTableBytes;
-    // device error word of the pipelined column kernel: the table slack after the
-    // last twiddle table (no table uses its final 256 bytes)
-    unsigned *err_flag = (unsigned *)((char *)scratch + kTableBytes - 256);
+    unsigned *err_flag = (unsigned *)((char *)scratch + kErrOffset);
 
     cudaError_t e;
-    if ((e = write_col_tables(f32, (int)n0, g0, tw0, st)) != cudaSuccess ||
+    if ((e = cudaMemsetAsync(err_flag, 0, sizeof(unsigned), st)) != cudaSuccess ||
+        (e = write_col_tables(f32, (int)n0, g0, tw0, st)) != cudaSuccess ||
         (e = write_col_tables(f32, (int)n1, g1, tw1, st)) != cudaSuccess ||
         (e = write_line_tables(f32, (int)m, gz.E, twz, st)) != cudaSuccess ||
         (e = (f32 ? twiddle_rot_launch_f32 : twiddle_rot_launch_f64)(rot, (int)n2, (int)m, st)) != cudaSuccess)
@@ -153,6 +187,7 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
         a.err = err_flag;
         a.early = 0;
         a.pf_stride = 0;
+        a.tickets = nullptr;
         a.stall_tx = 0;
         a.stage_polls = kStageWaitPolls;
         e = f32 ? col_launch_f32((int)n0, a, tiles, tw0, nullptr, nullptr, st) : col_launch_f64((int)n0, a, tiles, tw0, nullptr, nullptr, st);
@@ -174,6 +209,7 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
         a.err = err_flag;
         a.early = 0;
         a.pf_stride = 0;
+        a.tickets = nullptr;
         a.stall_tx = 0;
         a.stage_polls = kStageWaitPolls;
         a.tiles_per_field = 1;
@@ -193,4 +229,20 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
     z.max_blocks = 0;
     e = f32 ? zc2r_launch_f32((int)m, z, twz, rot, st) : zc2r_launch_f64((int)m, z, twz, rot, st);
     return e == cudaSuccess ? FFT3D_OK : FFT3D_ERR_CUDA;
+}
+
+extern "C" int fft3d_noalloc_status(int *device_error)
+{
+    if (!device_error) return FFT3D_ERR_NULL;
+    *device_error = 0;
+    void *scratch = nullptr;
+    if (scratch_for_current_device(&scratch) != cudaSuccess) return FFT3D_ERR_CUDA;
+    unsigned *err_flag = (unsigned *)((char *)scratch + kErrOffset);
+    unsigned v = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&v, err_flag, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && v) e = cudaMemset(err_flag, 0, sizeof(unsigned));
+    if (e != cudaSuccess) return FFT3D_ERR_CUDA;
+    *device_error = v ? 1 : 0;
+    return FFT3D_OK;
 }

@@ -96,3 +96,9 @@ def test_null_plan_calls(lib):
 def test_missing_library_fails_loudly(tmp_path):
     with pytest.raises(fft3d.FFT3DError):
         fft3d.load_library(str(tmp_path / "nope.so"))
+
+
+def test_diagnostics_reject_null_before_touching_cuda(lib):
+    D = ctypes.POINTER(ctypes.c_double)
+    assert lib.fft3d_noalloc_status(None) == fft3d.FFT3D_ERR_NULL
+    assert lib.fft3d_measure_fp64_peak(D(), D(), D()) == fft3d.FFT3D_ERR_NULL

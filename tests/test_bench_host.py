@@ -88,3 +88,40 @@ def test_clock_samples_median_and_reasons():
     s2.proc, s2.t = Proc(), Thread()
     s2.lines = ["0, 1500, 2070, 500.0, 0x40, Active, Not Active, Not Active, Not Active"]
     assert s2.stop()["reasons"] == ["hw_slowdown"]
+
+
+def test_reference_arm_labels_what_it_times():
+    """The reference arm times the FP64 oracle on a small grid; its `config`
+    must name that grid and dtype, matching its cpu_baseline sample."""
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
+                        "--ref-n", "32", "--steps", "1", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=300, cwd=bench.ROOT)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    cfg = line["config"]
+    assert cfg["grid"] == [32, 32, 32] and cfg["dtype"] == "f64" == line["dtype"]
+    assert "32x32x32" in cfg["workload"] and "FP64" in cfg["workload"]
+    assert "32^3" in line["cpu_baseline"]["sample"] and "FP64" in line["cpu_baseline"]["sample"]
+    assert "1024" not in json.dumps(cfg)  # not the GPU arm's workload
+    assert line["e2e"]["value"] == line["value"]
+
+
+def test_fp64_roofline_arithmetic():
+    stats = [{"name": "r2c.z", "total_ms": 80.0, "launches": 2, "bytes_per_launch": 1.0},
+             {"name": "c2r.x", "total_ms": 62.0, "launches": 2, "bytes_per_launch": 1.0}]
+    peak = {"fma_gflops": 1200.0, "add_gflops": 590.0, "mul_gflops": 600.0}
+    ops = {"r2c.z": {"dadd": 30.0, "dmul": 6.0, "dfma": 4.0}}
+    units = 1024 * 1024 * 513  # complex elements of one 1024^3 pass
+    r = bench.fp64_roofline(stats, ops, peak, units)
+    assert r["kernel"] == "r2c.z" and r["avg_launch_ms"] == 40.0
+    assert r["peak"] == 600.0  # FP64 instructions/s: the best of FMA (1200 / 2), add and multiply
+    assert math.isclose(r["achieved"], 40.0 * units / 40e-3 / 1e9, rel_tol=1e-3)
+    assert math.isclose(r["frac"], r["achieved"] / 600.0, rel_tol=1e-3)
+    assert math.isclose(r["achieved_gflops"], 44.0 * units / 40e-3 / 1e9, rel_tol=1e-3)
+    # op counts unknown (kernels changed since they were counted): no fraction
+    r2 = bench.fp64_roofline(stats, None, peak, units)
+    assert r2["achieved"] is None and r2["frac"] is None and r2["peak"] == 600.0
+    assert bench.fp64_roofline([], ops, peak, units) is None
