@@ -243,7 +243,7 @@ int fft3d_plan_info(fft3d_plan plan, int *fused_plane_pass);
  * (n0, n1, n2, dtype), with the same pass kernels, layouts, aliasing and
  * alignment rules, on `stream`.  Instead of plan memory it uses one static
  * device array of the library: FFT3D_NOALLOC_SCRATCH_BYTES for the
- * N0 x N1 scratch plane plus 128 KiB of twiddle tables.  So:
+ * N0 x N1 scratch plane plus 128.5 KiB of twiddle tables.  So:
  *   - every GPU that loads the library holds that array until the process
  *     exits;
  *   - all calls share it and it keeps the last call's contents; calls that

@@ -44,10 +44,13 @@ using namespace fft3d;
 
 namespace {
 
-// Twiddle space: four tables (axis 0, axis 1, axis 2 half length, R2C
-// rotation) of at most 2048 complex double entries each.
+// Twiddle space: three line tables (axis 0, axis 1, axis 2 half length) of
+// at most 2048 complex double entries each, then the contiguous-axis table
+// (at most 2 (1024 + 1) complex double entries, see z_table_elems), then
+// 256 bytes for the device error word.
 constexpr size_t kTableSlot = 2048 * 16;
-constexpr size_t kTableBytes = 4 * kTableSlot;
+constexpr size_t kZTableSlot = 129 * 256;  // 2 (1024 + 1) * 16 bytes, rounded up to 256
+constexpr size_t kTableBytes = 3 * kTableSlot + kZTableSlot + 256;
 constexpr size_t kPlaneBytes = FFT3D_NOALLOC_SCRATCH_BYTES;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kTableBytes + kPlaneBytes];
@@ -57,8 +60,7 @@ std::mutex g_setup_mu;
 void *g_scratch_ptr[kMaxDevices];      // device address of g_noalloc_scratch, per device
 CUcontext g_scratch_ctx[kMaxDevices];  // the context that address and the kernel set-up belong to
 
-// Offset of the device error word: the table slack after the last twiddle
-// table (no table uses its final 256 bytes).
+// Offset of the device error word, after the tables.
 constexpr size_t kErrOffset = kTableBytes - 256;
 
 typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
@@ -162,7 +164,7 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
         (e = write_col_tables(f32, (int)n0, g0, tw0, st)) != cudaSuccess ||
         (e = write_col_tables(f32, (int)n1, g1, tw1, st)) != cudaSuccess ||
         (e = write_line_tables(f32, (int)m, gz.E, twz, st)) != cudaSuccess ||
-        (e = (f32 ? twiddle_rot_launch_f32 : twiddle_rot_launch_f64)(rot, (int)n2, (int)m, st)) != cudaSuccess)
+        (e = write_z_table(f32, (int)n2, rot, st)) != cudaSuccess)
         return FFT3D_ERR_CUDA;
 
     const bool inplace = in_cplx == out_real;

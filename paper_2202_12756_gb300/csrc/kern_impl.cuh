@@ -470,6 +470,13 @@ inline cudaError_t fused_launch_t(const FusedArgs &a, const void *tw_y, const vo
             (typename cvec<R>::T *)out, n, count);                                              \
         return cudaGetLastError();                                                              \
     }                                                                                           \
+    cudaError_t twiddle_herm_launch_##SUF(void *out, int n, int count, cudaStream_t st)        \
+    {                                                                                           \
+        if (count <= 0) return cudaSuccess;                                                     \
+        twiddle_herm_kernel<R><<<(count + 255) / 256, 256, 0, st>>>(                           \
+            (typename cvec<R>::T *)out, n, count);                                              \
+        return cudaGetLastError();                                                              \
+    }                                                                                           \
     }
 
 #define FFT3D_CASE_FUSED_GEOM(N1, M) \

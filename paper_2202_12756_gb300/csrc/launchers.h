@@ -51,7 +51,8 @@ inline int col_table_elems(int L, const PassGeom &g)
     cudaError_t zc2r_launch_##SUF(int M, const ZArgs &a, const void *tw, const void *rot,           \
                                   cudaStream_t st);                                                  \
     cudaError_t twiddle_stage_launch_##SUF(void *out, int ns, int r, cudaStream_t st);             \
-    cudaError_t twiddle_rot_launch_##SUF(void *out, int n, int count, cudaStream_t st);
+    cudaError_t twiddle_rot_launch_##SUF(void *out, int n, int count, cudaStream_t st);             \
+    cudaError_t twiddle_herm_launch_##SUF(void *out, int n, int count, cudaStream_t st);
 
 FFT3D_DECLARE_LAUNCHERS(f32, float)
 FFT3D_DECLARE_LAUNCHERS(f64, double)
@@ -78,6 +79,16 @@ inline cudaError_t write_col_tables(bool f32, int L, const PassGeom &g, void *ds
     if (e != cudaSuccess) return e;
     void *rot = (char *)dst + (size_t)line_tw_size(L / 2, g.E) * (f32 ? 8 : 16);
     return f32 ? twiddle_rot_launch_f32(rot, L, L / 2 / g.E, st) : twiddle_rot_launch_f64(rot, L, L / 2 / g.E, st);
+}
+
+// Table of the contiguous-axis passes of an N2 = 2M point line (`rot` of
+// the z launchers): float lines take the R2C rotations exp(-2 pi i k / N2),
+// k < M; double lines take the [A, B] coefficient pairs of their Hermitian
+// post- / pre-process for k <= M (see twiddle_herm_kernel).
+inline size_t z_table_elems(bool f32, int m) { return f32 ? (size_t)m : 2 * ((size_t)m + 1); }
+inline cudaError_t write_z_table(bool f32, int n2, void *dst, cudaStream_t st)
+{
+    return f32 ? twiddle_rot_launch_f32(dst, n2, n2 / 2, st) : twiddle_herm_launch_f64(dst, n2, n2 / 2 + 1, st);
 }
 
 // Fused plane pass (float only): available for (N1, M) in

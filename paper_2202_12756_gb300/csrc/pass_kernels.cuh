@@ -953,6 +953,29 @@ __device__ __forceinline__ void zr2c_lines(const ZArgs &a, int64_t line0, unsign
             const C zm = (j == 0) ? v[(E - i) % E] : zp;
             emit(k, v[i], zm, z_rot<R, E, i>(rot_j, rot, k));
         });
+    } else if constexpr (sizeof(R) == 8) {
+        // Double lines (bound by FP64 issue): X[k] = A[k] Z[k] + B[k] conj(Z[M - k]),
+        // A = (1 - i r) / 2, B = (1 + i r) / 2 from the coefficient table (`rot`
+        // holds [A, B] pairs), 8 FP64 operations per element instead of 12; the
+        // output scale is applied only when it is not 1.
+        constexpr bool LR = pad_linear_reads<P>(NT);
+        constexpr bool LREV = P < 0 || NT % (1 << P) == 0;
+#pragma unroll
+        for (int i = 0; i < E; ++i) ex.put(pad_row<P, LR>(j, i * NT), v[i]);
+        ex.sync();
+        const bool unit = se == R(1) && sm == R(1);
+        static_for<0, E>([&](auto II) {
+            constexpr int i = decltype(II)::value;
+            const int k = j + i * NT;
+            const C z = ex.get(pad_row<P, LR>(j, i * NT));
+            const C zm = (i == 0 && j == 0) ? z : ex.get(pad_row<P, LREV>(M - j, -i * NT));
+            const C A = __ldg(rot + 2 * k), B = __ldg(rot + 2 * k + 1);
+            // A z + B conj(zm)
+            C x = cmake<C>(fma(A.x, z.x, fma(-A.y, z.y, fma(B.x, zm.x, B.y * zm.y))),
+                           fma(A.x, z.y, fma(A.y, z.x, fma(B.y, zm.x, -B.x * zm.y))));
+            if (!unit) x = cscale(x, k == 0 ? se : sm);
+            if (active) store_out(out + k, x);
+        });
     } else {
         constexpr bool LR = pad_linear_reads<P>(NT);
         constexpr bool LREV = P < 0 || NT % (1 << P) == 0;  // M - j - i NT stays linear in i
@@ -1053,16 +1076,29 @@ __device__ __forceinline__ void zc2r_lines(const ZArgs &a, int64_t line0, unsign
         static_for<0, E>([&](auto II) {
             constexpr int i = decltype(II)::value;
             const int k = j + i * NT;
-            const C x = ex.get(pad_row<P, LR>(j, i * NT));
-            const C y = ex.get(pad_row<P, LREV>(M - j, -i * NT));  // X[M - k]; k = 0 pairs with X[M]
-            v[i] = pre(k, x, y, z_rot<R, E, i>(rot_j, rot, k));
+            C x = ex.get(pad_row<P, LR>(j, i * NT));
+            C y = ex.get(pad_row<P, LREV>(M - j, -i * NT));  // X[M - k]; k = 0 pairs with X[M]
+            if constexpr (sizeof(R) == 8) {
+                // Double lines: conj Z[k] = 2 (A[k] conj(x) + B[k] y) with the
+                // coefficient table of the R2C lines (8 FP64 operations instead
+                // of 10); the factor 2 goes into the output scale below.
+                if (k == 0) {
+                    x = cmake<C>(we * x.x, R(0));
+                    y = cmake<C>(we * y.x, R(0));
+                }
+                const C A = __ldg(rot + 2 * k), B = __ldg(rot + 2 * k + 1);
+                v[i] = cmake<C>(fma(A.x, x.x, fma(A.y, x.y, fma(B.x, y.x, -B.y * y.y))),
+                                fma(A.y, x.x, fma(-A.x, x.y, fma(B.x, y.y, B.y * y.x))));
+            } else {
+                v[i] = pre(k, x, y, z_rot<R, E, i>(rot_j, rot, k));
+            }
         });
         ex.sync();
     }
 
     line_fft<R, M, E>(v, j, tw, ex);
 
-    const R s = R(a.scale_mid);
+    const R s = R(sizeof(R) == 8 ? 2.0 * a.scale_mid : a.scale_mid);
     C *out = (C *)((R *)a.real_out + l * a.real_pitch);
     if (active) {
 #pragma unroll
@@ -1134,6 +1170,23 @@ __global__ void twiddle_stage_kernel(typename cvec<R>::T *out, int ns, int r)
     double s, c;
     sincospi(2.0 * (double)p / (double)d, &s, &c);
     out[i] = cmake<C>(R(c), R(-s));
+}
+
+// Coefficients of the Hermitian post- / pre-process of double lines, for
+// k <= count - 1: with r = exp(-2 pi i k / n) = (cos t, -sin t),
+//   out[2k] = A = (1 - i r) / 2 = ((1 - sin t) / 2, -cos t / 2),
+//   out[2k + 1] = B = (1 + i r) / 2 = ((1 + sin t) / 2, cos t / 2),
+// computed in FP64 from sincospi (after exact reduction of k mod n).
+template <typename R>
+__global__ void twiddle_herm_kernel(typename cvec<R>::T *out, int n, int count)
+{
+    typedef typename cvec<R>::T C;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    double s, c;
+    sincospi(2.0 * (double)(k % n) / (double)n, &s, &c);
+    out[2 * k] = cmake<C>(R(0.5 - 0.5 * s), R(-0.5 * c));
+    out[2 * k + 1] = cmake<C>(R(0.5 + 0.5 * s), R(0.5 * c));
 }
 
 // rot[k] = exp(-2 pi i k / n), k < count (FP64 sincospi, rounded once)
