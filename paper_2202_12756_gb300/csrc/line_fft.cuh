@@ -442,34 +442,42 @@ __device__ __forceinline__ void line_exchange(typename cvec<R>::T *v, int j, Ex 
     }
 }
 
-template <typename R, int L, int E, int S, bool TWS, class Ex, class Hook>
+template <typename R, int L, int E, int S, bool TWS, class Ex, class Hook, class Tail>
 __device__ __forceinline__ void line_stages_from(typename cvec<R>::T *v, int j,
                                                  const typename cvec<R>::T *__restrict__ tw, Ex &ex,
-                                                 const Hook &hook)
+                                                 const Hook &hook, const Tail &tail)
 {
     if constexpr (S < line_nstages(L, E)) {
         line_stage_compute<R, L, E, S, TWS>(v, j, tw);
         if constexpr (S + 1 < line_nstages(L, E)) {
             if constexpr (S == 0) line_exchange<R, L, E, S>(v, j, ex, hook);
             else line_exchange<R, L, E, S>(v, j, ex, NoHook());
+            if constexpr (S + 2 == line_nstages(L, E)) tail();  // the last exchange is done with `ex`
         } else if constexpr (S == 0) {
             hook();
+            tail();
         }
-        line_stages_from<R, L, E, S + 1, TWS>(v, j, tw, ex, hook);
+        line_stages_from<R, L, E, S + 1, TWS>(v, j, tw, ex, hook, tail);
     }
 }
 
 // Forward FFT of a line held as v[i] = x[j + i NT]; result in the same slots.
-// `hook` runs once after the first exchange barrier (or after the only stage).
-// TWS: `tw` points to a copy of the twiddle table in shared memory.
-template <typename R, int L, int E, bool TWS = false, class Ex, class Hook = NoHook>
+// `hook` runs once after the first exchange barrier (or after the only
+// stage); `tail` runs once after the last exchange has ended on a barrier, so
+// that every thread's reads of the exchange buffer are complete (or after the
+// only stage).  TWS: `tw` points to a copy of the twiddle table in shared
+// memory.
+template <typename R, int L, int E, bool TWS = false, class Ex, class Hook = NoHook, class Tail = NoHook>
 __device__ __forceinline__ void line_fft(typename cvec<R>::T *v, int j,
                                          const typename cvec<R>::T *__restrict__ tw, Ex &ex,
-                                         const Hook &hook = Hook())
+                                         const Hook &hook = Hook(), const Tail &tail = Tail())
 {
     static_assert(line_plan_valid(L, E), "invalid line plan");
-    if constexpr (line_nstages(L, E) == 0) hook();
-    line_stages_from<R, L, E, 0, TWS>(v, j, tw, ex, hook);
+    if constexpr (line_nstages(L, E) == 0) {
+        hook();
+        tail();
+    }
+    line_stages_from<R, L, E, 0, TWS>(v, j, tw, ex, hook, tail);
 }
 
 }  // namespace fft3d

@@ -489,6 +489,191 @@ colpass_pipe_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64
     cp_async_wait_all();
 }
 
+// ------------------------------------------------------------ one-buffer pipelined column pass
+// Columns whose 16-column tile fills shared memory on its own (float L = 1536:
+// 192 KB, no room for a staging buffer beside a separate exchange buffer) run
+// a persistent kernel whose staging buffer is also the transform's exchange
+// buffer ([L][W] complex, as in colpass_kernel).  The next tile's copies can
+// start only once the last exchange is done with the buffer, so they overlap
+// the last radix stage and the stores of the current tile; the one-tile
+// kernel overlaps nothing of its own tile (one block per SM, each loading its
+// tile when it starts).  Staging (TMA modes 1 and 2, per-element cp.async
+// otherwise), tile order (static, or dynamic with a.tickets) and the bounded
+// tile waits are those of colpass_pipe_kernel.
+template <typename R, int L, int E, int W> __host__ __device__ constexpr size_t xstage_smem_bytes()
+{
+    return (size_t)stage_elems<typename cvec<R>::T, W, L>() * sizeof(typename cvec<R>::T) + 32 +
+           (size_t)line_tw_size(L, E) * sizeof(typename cvec<R>::T);
+}
+
+template <typename R, int L, int E, int W, bool INV>
+__global__ void __launch_bounds__(W *(L / E), 1)
+colpass_xstage_kernel(ColArgs a, const typename cvec<R>::T *__restrict__ tw, int64_t ntiles,
+                    const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap2)
+{
+    typedef typename cvec<R>::T C;
+    constexpr int NT = L / E;
+    constexpr int RSE = stage_row_elems<C, W>();
+    static_assert(L % (2 * kTmaBoxRows) == 0 && NT % 2 == 0 && (RSE * sizeof(C)) % 16 == 0, "staging layout");
+    static_assert(line_nstages(L, E) >= 2 && L * W <= stage_elems<C, W, L>(), "the exchange reuses the staging buffer");
+    extern __shared__ __align__(1024) unsigned char xstage_smem_raw[];
+    C *stage = (C *)xstage_smem_raw;
+    C *stage_odd = stage + L / 2 * W;  // mode 2: odd rows, W + 2 wide
+    uint64_t *mbar = (uint64_t *)(stage + stage_elems<C, W, L>());
+    int64_t *tslot = (int64_t *)(mbar + 2);  // dynamic order: tiles drawn one iteration ahead
+    C *tws = (C *)(mbar + 4);                // the block's copy of the twiddle table
+    constexpr int NTW = line_tw_size(L, E);
+    for (int i = threadIdx.x; i < NTW; i += blockDim.x) tws[i] = __ldg(tw + i);
+    const int c = threadIdx.x % W;
+    const int j = threadIdx.x / W;
+    ColEx<C, W> ex{stage, c};  // [L][W] over the staging buffer, once the tile is in registers
+    const uint32_t mb = smem_u32(mbar);
+    if (threadIdx.x == 0) {
+        mbar_init(mb, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+
+    // Start staging tile tt; returns its mode (0 cp.async, 1 or 2 TMA).
+    auto fill = [&](int64_t tt, const C *sp, int64_t ss) -> int {
+        const int mode = tt < a.tiles_main ? a.bulk : 0;
+        if (mode) {
+            if (threadIdx.x == 0) {
+                // order the block's earlier reads of the buffer before the async-proxy writes
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                if (mode == 1) {
+                    mbar_arrive_expect_tx(mb, (unsigned)(L * W * sizeof(C)) + a.stall_tx);
+                    int x, y0;
+                    if (a.axis == 0) {  // [B N0][N1 (M+1)]: the tile's flat columns, its field's rows
+                        const int64_t b = (uint32_t)tt / (uint32_t)a.tiles_per_field;
+                        x = (int)((tt - b * a.tiles_per_field) * W);
+                        y0 = (int)(b * a.n0);
+                    } else {            // [N0 N1][M+1]: plane k0, columns c0..
+                        const int64_t k0 = tt / a.tiles_per_plane;
+                        x = (int)((tt - k0 * a.tiles_per_plane) * W);
+                        y0 = (int)(k0 * a.n1);
+                    }
+#pragma unroll
+                    for (int b = 0; b < L / kTmaBoxRows; ++b)
+                        tma_load_2d(smem_u32(stage + b * kTmaBoxRows * W), &tmap, x, y0 + b * kTmaBoxRows, mb);
+                } else {
+                    mbar_arrive_expect_tx(mb, (unsigned)(L / 2 * (2 * W + 2) * sizeof(C)) + a.stall_tx);
+                    const int64_t k0 = tt / a.tiles_per_plane;
+                    const int c0 = (int)((tt - k0 * a.tiles_per_plane) * W);
+                    const int y0 = (int)(k0 * (a.n1 / 2));
+#pragma unroll
+                    for (int b = 0; b < L / 2 / kTmaBoxRows; ++b) {
+                        tma_load_2d(smem_u32(stage + b * kTmaBoxRows * W), &tmap, c0, y0 + b * kTmaBoxRows, mb);
+                        tma_load_2d(smem_u32(stage_odd + b * kTmaBoxRows * (W + 2)), &tmap2, c0 + (int)a.m,
+                                    y0 + b * kTmaBoxRows, mb);
+                    }
+                }
+            }
+        } else {
+            const C *sj = sp + (int64_t)j * ss;
+            const int64_t sstep = (int64_t)NT * ss;
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                C *dst = stage + (j + i * NT) * RSE + c;
+                if (sizeof(C) == 8) cp_async_8(dst, sj + i * sstep);
+                else cp_async_16(dst, sj + i * sstep);
+            }
+            cp_async_commit();
+        }
+        return mode;
+    };
+
+    // Tile order.  Static: t = blockIdx.x + q gridDim.x, so that at any moment
+    // the blocks work on neighbouring tiles, whose rows share DRAM pages
+    // (measured on GB300: giving each block runs of 2, 4 or 8 consecutive
+    // tiles instead slows the y-pass by 15, 27 and 45%, and runs of 2 to all
+    // of a block's tiles gain nothing in the x-pass).  Dynamic (a.tickets):
+    // a block's first two tiles are blockIdx.x and blockIdx.x + gridDim.x,
+    // and each later one is 2 gridDim.x + a ticket drawn from *a.tickets
+    // (zeroed before the launch), one iteration ahead so that the atomic's
+    // latency stays off the tile's path: slots tslot[q & 1] alternate, each
+    // written after one staging barrier and read after the next.  Tickets go
+    // out in time order, so a block whose next tile is past the end has no
+    // later tile pending.  Blocks that run faster take more tiles, and the
+    // pass no longer waits for the slowest SM's share.
+    const bool dyn = a.tickets != nullptr;
+    // Registers are tight here (1024 threads), so a tile's source and
+    // destination are decoded where they are used, not held across the transform.
+    int64_t t = blockIdx.x;
+    int mode = 0;
+    if (t < ntiles) {
+        C *sp = nullptr, *dp = nullptr;
+        int64_t ss = 0, ds = 0;
+        col_decode<C, W>(a, t, c, sp, ss, dp, ds);
+        mode = fill(t, sp, ss);
+    }
+    for (int q = 0; t < ntiles; ++q) {
+        if (mode) {
+            const bool ok = mbar_wait_bounded(mb, phase, a.stage_polls);
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) atomicOr(a.err, 1u);
+                mbar_wait_bounded(mb, phase, a.stage_polls);  // copies still in flight
+                return;
+            }
+            phase ^= 1u;
+        } else {
+            cp_async_wait_all();  // this thread's copies of tile t have landed
+            if (dyn) __syncthreads();  // orders the tile slots (written after the previous barrier)
+        }
+        const int64_t tn = (dyn && q > 0) ? tslot[(q - 1) & 1] : t + gridDim.x;
+        if (dyn && threadIdx.x == 0) tslot[q & 1] = 2 * (int64_t)gridDim.x + atomicAdd(a.tickets, 1u);
+        C v[E];
+        if (mode == 2) {
+            // rows j + i NT (NT even) share the parity of j
+            const C *base = (j & 1) ? stage_odd + (j >> 1) * (W + 2) + c + 1 : stage + (j >> 1) * W + c;
+            const int step = (j & 1) ? (NT / 2) * (W + 2) : (NT / 2) * W;
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                v[i] = base[i * step];
+                if (INV) v[i] = cswap(v[i]);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                v[i] = stage[(j + i * NT) * RSE + c];
+                if (INV) v[i] = cswap(v[i]);
+            }
+        }
+        int moden = 0;
+        auto next = [&]() {
+            if (tn < ntiles) {
+                C *spn = nullptr, *dpn = nullptr;
+                int64_t ssn = 0, dsn = 0;
+                col_decode<C, W>(a, tn, c, spn, ssn, dpn, dsn);
+                moden = fill(tn, spn, ssn);
+            }
+        };
+        // every thread has its elements of tile t in registers before the exchanges
+        // overwrite the buffer; tile tn is staged once the last exchange is done with it
+        __syncthreads();
+        line_fft<R, L, E, true>(v, j, tws, ex, NoHook(), next);
+        {
+            C *sp = nullptr, *dp = nullptr;
+            int64_t ss = 0, ds = 0;
+            if (col_decode<C, W>(a, t, c, sp, ss, dp, ds)) {
+                C *dj = dp + (int64_t)j * ds;
+                const int64_t dstep = (int64_t)NT * ds;
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    C o = v[i];
+                    if (INV) o = cswap(o);
+                    store_out(dj + i * dstep, o);
+                }
+            }
+        }
+        t = tn;
+        mode = moden;
+    }
+    cp_async_wait_all();
+}
+
+
 // ------------------------------------------------------------ column pairs
 // Columns too long for one SM to hold W = 16 of them (L = 2048 float: a
 // 256 KB tile) run on a cluster of two CTAs.  CTA r of the pair holds the

@@ -59,7 +59,7 @@ def test_plans_without_fused_pass_report_no_error():
     assert plan.status() == 0
 
 
-@pytest.mark.parametrize("shape", [(1024, 16, 32), (8, 1024, 64), (2048, 16, 32), (8, 2048, 64)],
+@pytest.mark.parametrize("shape", [(1024, 16, 32), (8, 1024, 64), (2048, 16, 32), (8, 2048, 64), (1536, 16, 32)],
                          ids=lambda s: "x".join(map(str, s)))
 def test_pipelined_tile_wait_reports_and_recovers(shape):
     """The pipelined column kernel waits on an mbarrier for the TMA copies of
@@ -70,7 +70,8 @@ def test_pipelined_tile_wait_reports_and_recovers(shape):
     even/odd row-pair copies of an odd row pitch; (2048, 16, 32): the x-pass
     on clusters of two CTAs, which meet at a final cluster barrier whichever
     of their waits runs out; (8, 2048, 64): the 2048-point y-pass on one SM
-    per 8-column tile.)"""
+    per 8-column tile; (1536, 16, 32): the 1536-point x-pass on the kernel
+    whose staging buffer is also its exchange buffer.)"""
     import torch
     import paper_2202_12756_gb300 as fft3d
     plan = fft3d.Plan(shape, torch.float32)

@@ -228,6 +228,20 @@ def test_tma_staged_column_passes(shape):
         check_pair(shape, "f32", inplace, seed=9)
 
 
+@pytest.mark.parametrize("shape", [(1536, 16, 32), (1536, 24, 24), (6, 1536, 64), (4, 1536, 96), (1536, 1536, 32)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_one_buffer_pipelined_column_passes(shape):
+    """The float x-pass of 1536 points runs on the persistent kernel whose
+    staging buffer is also the transform's exchange buffer: tiles staged by
+    TMA (1536 x 16 x 32: 16 * 17 = 272 columns, 17 full tiles; 1536 x 1536 x
+    32 with the one-tile y-pass of the same length) or per element with a
+    ragged last tile (24 * 13 = 312 columns).  The 1536-point y-passes of
+    (6, 1536, 64) and (4, 1536, 96) stay on the one-tile kernel.  Both
+    directions, element by element against the oracle."""
+    for inplace in (False, True):
+        check_pair(shape, "f32", inplace, seed=23)
+
+
 @pytest.mark.parametrize("shape", [(2048, 64, 64), (2048, 24, 24), (32, 2048, 64), (3, 2048, 192)],
                          ids=lambda s: "x".join(map(str, s)))
 def test_cta_pair_column_passes(shape):
