@@ -13,7 +13,7 @@ namespace fft3d {
 #define FFT3D_COL_MAXT_F32 1024
 #endif
 #ifndef FFT3D_COL_MAXT_F64
-#define FFT3D_COL_MAXT_F64 512
+#define FFT3D_COL_MAXT_F64 256
 #endif
 #ifndef FFT3D_Z_THREADS
 #define FFT3D_Z_THREADS 256
@@ -21,7 +21,12 @@ namespace fft3d {
 
 // Block-size cap of a one-tile-per-block column pass: 1024 threads for float
 // (so a tile row stays one 128-byte segment even at 24 elements per thread,
-// at the price of a few spilled registers there), 512 / 256 for double.
+// at the price of a few spilled registers there), 256 for double.  Double
+// passes are bound by FP64 issue, not by HBM, so narrower tiles (64-byte row
+// segments of 4 columns at 1024 points) cost them nothing in DRAM terms and
+// let two blocks share an SM, which hides each tile's loads and barriers:
+// measured on GB300 at 1024^3, FP64 column passes 31.5-32.0 -> 30.2-30.3 ms
+// (a 128-thread cap: 30.2 ms; 512 threads, one block per SM: the former).
 template <typename R, int L> __host__ __device__ constexpr int col_max_threads()
 {
     return sizeof(R) == 4 ? FFT3D_COL_MAXT_F32 : (line_E(L) <= 16 ? FFT3D_COL_MAXT_F64 : 256);
