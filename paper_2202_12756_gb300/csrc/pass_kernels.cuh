@@ -1170,7 +1170,7 @@ __device__ __forceinline__ void zr2c_lines(const ZArgs &a, int64_t line0, unsign
         static_for<0, E>([&](auto II) {
             constexpr int i = decltype(II)::value;
             const int k = j + i * NT;
-            const C z = ex.get(pad_row<P, LR>(j, i * NT));
+            const C z = v[i];  // this thread's own Z[k] is still in registers
             const C zm = ex.get(pad_row<P, LREV>(M - j, -i * NT));  // Z[M - k]; k = 0 reads index M
             emit(k, z, (i == 0 && j == 0) ? z : zm, z_rot<R, E, i>(rot_j, rot, k));
         });
@@ -1261,7 +1261,9 @@ __device__ __forceinline__ void zc2r_lines(const ZArgs &a, int64_t line0, unsign
         static_for<0, E>([&](auto II) {
             constexpr int i = decltype(II)::value;
             const int k = j + i * NT;
-            C x = ex.get(pad_row<P, LR>(j, i * NT));
+            // float lines take their own X[k] from registers (one shared-memory read
+            // fewer per element for the L1-bound two-warp lines)
+            C x = sizeof(R) == 4 ? v[i] : ex.get(pad_row<P, LR>(j, i * NT));
             C y = ex.get(pad_row<P, LREV>(M - j, -i * NT));  // X[M - k]; k = 0 pairs with X[M]
             if constexpr (sizeof(R) == 8) {
                 // Double lines: conj Z[k] = 2 (A[k] conj(x) + B[k] y) with the
