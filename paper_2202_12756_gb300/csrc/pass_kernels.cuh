@@ -14,8 +14,10 @@
 //               Step 1; or axis 0, the slowest axis of Step 5).  A tile of W
 //               adjacent columns is read with the lanes of a warp across the
 //               columns, so every row of the tile is one coalesced segment of
-//               W * sizeof(complex) = 128 bytes; the column FFTs exchange
-//               through shared memory.  The x-pass does in one read and one
+//               W * sizeof(complex) = 128 bytes (64 where the tile is
+//               narrowed: 2048-point float columns on one SM, FP64 columns
+//               of 1024 points); the column FFTs exchange through shared
+//               memory.  The x-pass does in one read and one
 //               write what the paper does with two transposes and an
 //               all-to-all (Steps 2-5): no transposed copy of the array exists.
 #pragma once
@@ -314,8 +316,9 @@ template <typename R, int L, int E, int W> __host__ __device__ constexpr size_t 
 // (real / imaginary) buffer.  A tile wait that runs out raises *a.err and the
 // block leaves after a second bounded wait.  The twiddle table is copied to
 // shared memory once per block (a thread's twiddles are the same in every
-// tile).  The tile is W = 16 float2 columns: 128-byte row segments, which
-// HBM serves at about twice the rate of 64-byte ones at this row stride.
+// tile).  The tile is W = 16 float2 columns (8 at 2048 points, where 16
+// would not fit beside the staging buffer): 128-byte row segments, which
+// HBM serves at about twice the rate of 64-byte ones at large row strides.
 // With EARLY the next tile is staged as soon as the current one is in
 // registers (one barrier more per tile) rather than after the first exchange
 // barrier; which is faster depends on the access pattern (ColArgs::early,
