@@ -184,6 +184,42 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+class HostBuffers:
+    """Page-locked host arrays for the end-to-end runs: anonymous memory
+    (transparent huge pages requested) registered with cudaHostRegister.
+    Measured on these boxes after other GPU work in the same machine, copies
+    in both directions at once between HBM and cudaHostAlloc-pinned arrays of
+    4 GB fell to 164 GB/s in total, against 343 GB/s for registered ones."""
+
+    def __init__(self):
+        self.held = []
+
+    def empty(self, shape):
+        import mmap
+        import numpy as np
+        import torch
+        nbytes = int(np.prod(shape)) * 4
+        m = mmap.mmap(-1, nbytes, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
+        if hasattr(mmap, "MADV_HUGEPAGE"):
+            m.madvise(mmap.MADV_HUGEPAGE)
+        a = np.frombuffer(m, dtype=np.float32).reshape(shape)
+        a[...] = 0.0  # touch every page before it is locked
+        rc = torch.cuda.cudart().cudaHostRegister(a.ctypes.data, nbytes, 0)
+        if int(rc) != 0:
+            raise RuntimeError(f"cudaHostRegister failed ({rc})")
+        self.held.append((m, a))
+        return torch.from_numpy(a)
+
+    def release(self):
+        import torch
+        torch.cuda.synchronize()
+        for m, a in self.held:
+            torch.cuda.cudart().cudaHostUnregister(a.ctypes.data)
+        for m, a in self.held:
+            del a
+        self.held = []
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -476,9 +512,11 @@ def run_ours(args):
     # in HBM); (b) copy engines move the field into a dense device array and
     # the result back out (cudaMemcpyAsync on the pair's stream) around the
     # device-resident transforms, so the SMs stay free for another field.
-    host_in = torch.empty(grid, dtype=torch.float32, pin_memory=True)
+    hostbufs = HostBuffers()
+    host_in = hostbufs.empty(grid)
     host_in.copy_(buf32[..., :n])
-    host_out = torch.empty_like(host_in, pin_memory=True)
+    host_out = hostbufs.empty(grid)
+    extra_outs = []  # the other streams' result arrays, reused across the runs
     del buf32
     # enough pairs that filling and draining three streams' pipelines is a small part of the timed region
     e2e_steps = max(24, 2 * max(1, args.steps // 20))
@@ -489,7 +527,9 @@ def run_ours(args):
         copies: through a dense device array per stream and the copy engines."""
         plans = [plan32] + [fft3d.Plan(grid, torch.float32, dev) for _ in range(nstreams - 1)]
         cplx = [p.empty_complex() for p in plans]
-        outs = [host_out] + [torch.empty_like(host_in, pin_memory=True) for _ in range(nstreams - 1)]
+        while len(extra_outs) < nstreams - 1:
+            extra_outs.append(hostbufs.empty(grid))
+        outs = [host_out] + extra_outs[:nstreams - 1]
         dreal = [torch.empty(grid, dtype=torch.float32, device=dev) for _ in range(nstreams)] if copies else None
         # every field on a stream of its own; the timing events go on the current stream
         main = torch.cuda.current_stream(dev)
@@ -524,7 +564,7 @@ def run_ours(args):
         b.record(main)
         torch.cuda.synchronize(dev)
         ms = max_over_ranks(a.elapsed_time(b), pg, dev) / e2e_steps
-        del plans, cplx, outs[1:], dreal
+        del plans, cplx, outs, dreal
         torch.cuda.empty_cache()
         return ms
 
@@ -562,7 +602,8 @@ def run_ours(args):
                 "ms_per_step_one_stream": round(ms_e2e_1, 3), "ms_per_step_two_streams": round(ms_e2e_2, 3),
                 "ms_per_step_copies_two_streams": round(ms_e2e_c2, 3),
                 "ms_per_step_copies_three_streams": round(ms_e2e_c3, 3),
-                "how": "each pair starts from the field in pinned host memory and ends with the result there; "
+                "how": "each pair starts from the field in page-locked host memory (anonymous memory registered with "
+                       "cudaHostRegister) and ends with the result there; "
                        "either the forward's first pass reads the host field over the CPU-GPU link and the "
                        "inverse's last pass writes the result back (fft3d_exec_r2c / fft3d_exec_c2r_overwrite "
                        "with host pointers; one or two streams), or cudaMemcpyAsync moves the field into a dense "
@@ -578,7 +619,8 @@ def run_ours(args):
         line["torch_fft_reference"] = torch_ref
     rt = round_trip_error(plan32, host_in, host_out)
     line["fp32_round_trip_rel_l2"] = rt
-    del host_in, host_out
+    del host_in, host_out, extra_outs
+    hostbufs.release()
     if world == 1 and not args.no_configs:
         del plan64, plan32
         torch.cuda.empty_cache()
