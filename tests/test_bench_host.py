@@ -125,3 +125,17 @@ def test_fp64_roofline_arithmetic():
     r2 = bench.fp64_roofline(stats, None, peak, units)
     assert r2["achieved"] is None and r2["frac"] is None and r2["peak"] == 600.0
     assert bench.fp64_roofline([], ops, peak, units) is None
+
+
+def test_copy_streams_that_fit(tmp_path):
+    """The copy-engine end-to-end runs lock (streams + 1) host fields per rank
+    and stay within half of MemAvailable."""
+    gib = 1024 ** 3
+    info = tmp_path / "meminfo"
+    info.write_text("MemTotal:       999999999 kB\nMemAvailable:   %d kB\n" % (200 * 1024 * 1024))
+    field = 4 * gib  # one dense 1024^3 FP32 field
+    assert bench.copy_streams_that_fit(field, 1, str(info)) == 3    # 16 GiB <= 100 GiB
+    assert bench.copy_streams_that_fit(field, 8, str(info)) == 2    # 128 GiB > 100, 96 GiB fits
+    assert bench.copy_streams_that_fit(field, 16, str(info)) == 0   # neither fits
+    assert bench.copy_streams_that_fit(field, 1, str(tmp_path / "missing")) == 2
+    assert bench.io_bytes_of((1024, 1024, 1024)) == field
