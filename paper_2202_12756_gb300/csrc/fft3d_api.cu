@@ -119,12 +119,23 @@ template <class F> int run_pass(fft3d_plan p, int kind, cudaStream_t st, F &&lau
     if (p->profiling) {
         a = take_event(p);
         b = take_event(p);
-        if (!a || !b) return set_err(p, FFT3D_ERR_CUDA, "cudaEventCreate failed");
-        cudaError_t e = cudaEventRecord(a, st);
-        if (e != cudaSuccess) return set_err(p, FFT3D_ERR_CUDA, "cudaEventRecord", e);
+        cudaError_t e = (a && b) ? cudaEventRecord(a, st) : cudaErrorMemoryAllocation;
+        if (e != cudaSuccess) {
+            // events that were taken go back to the pool
+            if (a) p->pool.push_back(a);
+            if (b) p->pool.push_back(b);
+            return set_err(p, FFT3D_ERR_CUDA, (a && b) ? "cudaEventRecord" : "cudaEventCreate", e);
+        }
     }
+    auto release = [&] {
+        if (p->profiling) {
+            p->pool.push_back(a);
+            p->pool.push_back(b);
+        }
+    };
     cudaError_t e = launch();
     if (e != cudaSuccess) {
+        release();
         char what[64];
         snprintf(what, sizeof(what), "launch of pass %s", kPassName[kind]);
         return set_err(p, FFT3D_ERR_CUDA, what, e);
@@ -132,7 +143,10 @@ template <class F> int run_pass(fft3d_plan p, int kind, cudaStream_t st, F &&lau
     ++p->launches;
     if (p->profiling) {
         e = cudaEventRecord(b, st);
-        if (e != cudaSuccess) return set_err(p, FFT3D_ERR_CUDA, "cudaEventRecord", e);
+        if (e != cudaSuccess) {
+            release();
+            return set_err(p, FFT3D_ERR_CUDA, "cudaEventRecord", e);
+        }
         p->pending.push_back({kind, a, b});
     }
     return FFT3D_OK;
