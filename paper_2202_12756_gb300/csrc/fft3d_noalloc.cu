@@ -45,7 +45,7 @@ using namespace fft3d;
 namespace {
 
 // Twiddle space: three line tables (axis 0, axis 1, axis 2 half length) of
-// at most 2048 complex double entries each, then the contiguous-axis table
+// at most 32 KB each (checked per call), then the contiguous-axis table
 // (at most 2 (1024 + 1) complex double entries, see z_table_elems), then
 // 256 bytes for the device error word.
 constexpr size_t kTableSlot = 2048 * 16;
@@ -147,6 +147,11 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
     if (!(f32 ? col_geom_f32((int)n0, 0, &g0) : col_geom_f64((int)n0, 0, &g0)) ||
         !(f32 ? col_geom_f32((int)n1, 1, &g1) : col_geom_f64((int)n1, 1, &g1)) ||
         !(f32 ? z_geom_f32((int)(n2 / 2), &gz) : z_geom_f64((int)(n2 / 2), &gz)))
+        return FFT3D_ERR_SIZE;
+    // every table must fit its slot (the largest, FP64 2048-point columns, takes 32512 of 32768 bytes)
+    if ((size_t)col_table_elems((int)n0, g0) * csize > kTableSlot ||
+        (size_t)col_table_elems((int)n1, g1) * csize > kTableSlot ||
+        (size_t)line_tw_size((int)m, gz.E) * csize > kTableSlot || z_table_elems(f32, (int)m) * csize > kZTableSlot)
         return FFT3D_ERR_SIZE;
 
     void *scratch = nullptr;
