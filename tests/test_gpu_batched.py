@@ -21,6 +21,7 @@ SHAPES = [
     (2, 8, 1024, 64),    # FP32 y-pass: pipelined kernel, even/odd row-pair TMA maps (odd pitch 33)
     (2, 2048, 16, 32),   # FP32 x-pass of 2048 points: CTA pairs, row-parity map over both fields' rows
     (2, 4, 2048, 64),    # FP32 y-pass of 2048 points: pipelined kernel on 8-column tiles over both fields' planes
+    (2, 1536, 8, 16),    # FP32 x-pass of 1536 points: one-buffer kernel, TMA rows of both fields
     (4, 6, 8, 12),
     (3, 1, 16, 32),      # N0 = 1: no x-pass
     (2, 32, 1, 16),      # N1 = 1: no y-pass
