@@ -1005,8 +1005,13 @@ struct ZArgs {
 // exchange fewer, and one warp per line up to M = 1024) doubles the registers
 // of a thread; measured on GB300 it halves the resident warps and runs 25%
 // slower at M = 512, and at M = 1024 (150-170 registers, one block per SM)
-// 45% slower.
-template <typename R, int M> __host__ __device__ constexpr int z_E() { return line_E(M); }
+// 45% slower.  Double lines of 512 points, bound by FP64 issue, take 8
+// (radix 8 x 8 x 8: about 28 FP64 operations per point against 28.75 for
+// 16 x 16 x 2; measured at 1024^3 the FP64 z-passes 36.6 -> 36.0 ms).
+template <typename R, int M> __host__ __device__ constexpr int z_E()
+{
+    return (sizeof(R) == 8 && M == 512) ? 8 : line_E(M);
+}
 
 // Per-line shared-memory exchange with one padding slot every 2^P elements:
 // P = 4 makes the stride-16 writes of a radix-16 first stage conflict-free;
