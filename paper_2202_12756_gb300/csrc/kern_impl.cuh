@@ -78,7 +78,15 @@ template <int L> __host__ __device__ constexpr int pair_E() { return 32; }
 __host__ __device__ constexpr bool pair_axis(int axis) { return axis >= 0 && ((FFT3D_PAIR_AXES >> axis) & 1) != 0; }
 constexpr int kPairW = 16;  // columns of a CTA-pair tile (128-byte float rows)
 
-template <typename R, int L> __host__ __device__ constexpr int col_E() { return col_pipe<R, L>() ? 32 : line_E(L); }
+// Elements per thread of a column pass: 32 in the pipelined kernel, else the
+// default plan of the length; double columns of 512 points, bound by FP64
+// issue, take 8 (radix 8 x 8 x 8: about 28 FP64 operations per point
+// against 28.75 for 16 x 16 x 2; measured at 512^3 the FP64 column passes
+// 3.43 -> 3.34 ms, on 4-column tiles).
+template <typename R, int L> __host__ __device__ constexpr int col_E()
+{
+    return col_pipe<R, L>() ? 32 : ((sizeof(R) == 8 && L == 512) ? 8 : line_E(L));
+}
 
 // Columns per tile: one 128-byte segment per row (16 float2 or 8 double2),
 // halved while the block would exceed its thread cap or, for the one-tile
@@ -90,7 +98,7 @@ template <typename R, int L> __host__ __device__ constexpr int col_W()
         while (w > 1 && w * (L / 32) > 512) w /= 2;
         return w;
     }
-    while (w > 1 && (w * line_NT(L) > col_max_threads<R, L>() ||
+    while (w > 1 && (w * (L / col_E<R, L>()) > col_max_threads<R, L>() ||
                      (size_t)L * w * sizeof(typename cvec<R>::T) > 200 * 1024))
         w /= 2;
     return w;
