@@ -543,7 +543,7 @@ int fft3d_plan_create_batched(fft3d_plan *out, int64_t batch, int64_t n0, int64_
     {
         const size_t s0 = align256((size_t)col_table_elems((int)n0, p->g0) * p->csize + 16);
         const size_t s1 = align256((size_t)col_table_elems((int)n1, p->g1) * p->csize + 16);
-        const size_t sz = align256((size_t)line_tw_size((int)p->m, p->gz.E) * p->csize + 16);
+        const size_t sz = align256((size_t)line_tw_size(z_line_points((int)p->m, p->gz), p->gz.E) * p->csize + 16);
         const size_t sr = align256(z_table_elems(f32, (int)p->m) * p->csize);
         const size_t sf = p->fused_ok ? align256((size_t)line_tw_size((int)n1, p->gf.E) * p->csize + 16) : 0;
         e = cudaMalloc(&p->tw, s0 + s1 + sz + sr + sf);
@@ -559,7 +559,7 @@ int fft3d_plan_create_batched(fft3d_plan *out, int64_t batch, int64_t n0, int64_
         p->tw1f = base + s0 + s1 + sz + sr;
         if ((e = write_col_tables(f32, (int)n0, p->g0, base, 0)) != cudaSuccess ||
             (e = write_col_tables(f32, (int)n1, p->g1, base + s0, 0)) != cudaSuccess ||
-            (e = write_line_tables(f32, (int)p->m, p->gz.E, base + s0 + s1, 0)) != cudaSuccess ||
+            (e = write_line_tables(f32, z_line_points((int)p->m, p->gz), p->gz.E, base + s0 + s1, 0)) != cudaSuccess ||
             (e = write_z_table(f32, (int)n2, base + s0 + s1 + sz, 0)) != cudaSuccess ||
             (p->fused_ok && (e = write_line_tables(f32, (int)n1, p->gf.E, base + s0 + s1 + sz + sr, 0)) != cudaSuccess)) {
             rc = FFT3D_ERR_CUDA;

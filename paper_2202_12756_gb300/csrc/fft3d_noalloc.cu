@@ -151,7 +151,8 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
     // every table must fit its slot (the largest, FP64 2048-point columns, takes 32512 of 32768 bytes)
     if ((size_t)col_table_elems((int)n0, g0) * csize > kTableSlot ||
         (size_t)col_table_elems((int)n1, g1) * csize > kTableSlot ||
-        (size_t)line_tw_size((int)m, gz.E) * csize > kTableSlot || z_table_elems(f32, (int)m) * csize > kZTableSlot)
+        (size_t)line_tw_size(z_line_points((int)m, gz), gz.E) * csize > kTableSlot ||
+        z_table_elems(f32, (int)m) * csize > kZTableSlot)
         return FFT3D_ERR_SIZE;
 
     void *scratch = nullptr;
@@ -168,7 +169,7 @@ extern "C" int fft3d_exec_c2r_noalloc(const void *in_cplx, void *out_real, int64
     if ((e = cudaMemsetAsync(err_flag, 0, sizeof(unsigned), st)) != cudaSuccess ||
         (e = write_col_tables(f32, (int)n0, g0, tw0, st)) != cudaSuccess ||
         (e = write_col_tables(f32, (int)n1, g1, tw1, st)) != cudaSuccess ||
-        (e = write_line_tables(f32, (int)m, gz.E, twz, st)) != cudaSuccess ||
+        (e = write_line_tables(f32, z_line_points((int)m, gz), gz.E, twz, st)) != cudaSuccess ||
         (e = write_z_table(f32, (int)n2, rot, st)) != cudaSuccess)
         return FFT3D_ERR_CUDA;
 

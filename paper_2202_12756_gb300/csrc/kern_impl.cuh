@@ -147,7 +147,11 @@ template <typename R, int M> inline void z_geom_t(PassGeom *g)
     g->per_block = LPB;
     g->E = z_E<R, M>();
     g->persistent = 0;
-    g->smem = (size_t)LPB * zline_smem_elems<M, z_E<R, M>()>() * sizeof(typename cvec<R>::T);
+    // paired lines: one buffer of the 2M-point transform per pair
+    g->pair = z_paired<R, M>() ? 1 : 0;
+    g->smem = (z_paired<R, M>() ? (size_t)(LPB / 2) * zline_smem_elems<2 * M, z_E<R, M>()>()
+                                : (size_t)LPB * zline_smem_elems<M, z_E<R, M>()>()) *
+              sizeof(typename cvec<R>::T);
 }
 
 template <typename R, int L> inline cudaError_t col_prepare_t()

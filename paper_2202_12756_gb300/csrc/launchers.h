@@ -81,6 +81,10 @@ inline cudaError_t write_col_tables(bool f32, int L, const PassGeom &g, void *ds
     return f32 ? twiddle_rot_launch_f32(rot, L, L / 2 / g.E, st) : twiddle_rot_launch_f64(rot, L, L / 2 / g.E, st);
 }
 
+// Points of a z-pass line transform of half length m with geometry gz: m,
+// or 2m when two real lines share one complex transform (gz.pair).
+inline int z_line_points(int m, const PassGeom &gz) { return gz.pair ? 2 * m : m; }
+
 // Table of the contiguous-axis passes of an N2 = 2M point line (`rot` of
 // the z launchers): float lines take the R2C rotations exp(-2 pi i k / N2),
 // k < M; double lines take the [A, B] coefficient pairs of their Hermitian

@@ -1005,13 +1005,14 @@ struct ZArgs {
 // exchange fewer, and one warp per line up to M = 1024) doubles the registers
 // of a thread; measured on GB300 it halves the resident warps and runs 25%
 // slower at M = 512, and at M = 1024 (150-170 registers, one block per SM)
-// 45% slower.  Double lines of 512 points, bound by FP64 issue, take 8
-// (radix 8 x 8 x 8: about 28 FP64 operations per point against 28.75 for
-// 16 x 16 x 2; measured at 1024^3 the FP64 z-passes 36.6 -> 36.0 ms).
-template <typename R, int M> __host__ __device__ constexpr int z_E()
-{
-    return (sizeof(R) == 8 && M == 512) ? 8 : line_E(M);
-}
+// 45% slower.
+// Double lines of N2 = 1024 points (M = 512), bound by FP64 issue, run two
+// lines per complex transform of N2 points (z_paired, zr2c_pairs /
+// zc2r_pairs below; 16 elements per thread, radix 16 x 16 x 4): about 33.9
+// FP64 operations per element against 36.4 for the half-length scheme on
+// radix 8 x 8 x 8; measured at 1024^3 the FP64 z-passes 36.1 -> 34.5 ms.
+template <typename R, int M> __host__ __device__ constexpr bool z_paired() { return sizeof(R) == 8 && M == 512; }
+template <typename R, int M> __host__ __device__ constexpr int z_E() { return z_paired<R, M>() ? 16 : line_E(M); }
 
 // Per-line shared-memory exchange with one padding slot every 2^P elements:
 // P = 4 makes the stride-16 writes of a radix-16 first stage conflict-free;
@@ -1301,6 +1302,135 @@ __device__ __forceinline__ void zc2r_lines(const ZArgs &a, int64_t line0, unsign
     }
 }
 
+// Two real lines per complex transform (double, z_paired).  Lines l and
+// l + 1 (l even) are read as z[n] = x_l[n] + i x_{l+1}[n], n < N = 2M, and
+// transformed once: Z = DFT_N(z).  Since both lines are real, their spectra
+// follow from Z and its mirror:
+//   X_l[k] = (Z[k] + conj Z[N - k]) / 2,  X_{l+1}[k] = (Z[k] - conj Z[N - k]) / 2i,
+// for k <= M (4 FP64 operations per output value, the 1/2 folded into the
+// output scale), against the half-length scheme's rotation post-process.  A
+// pair takes N / E threads; thread j holds Z[j + i NT] and reads Z[N - k]
+// of the partner thread through the line's shared-memory buffer.  With an
+// odd line count the last pair's second line is zero and not written.
+template <typename R, int M, int E, int LPB>
+__device__ __forceinline__ void zr2c_pairs(const ZArgs &a, int64_t line0, unsigned char *smem,
+                                           const typename cvec<R>::T *__restrict__ tw)
+{
+    typedef typename cvec<R>::T C;
+    constexpr int N = 2 * M;
+    constexpr int NT = N / E;
+    constexpr int PPB = LPB / 2;  // pairs per block
+    constexpr int P = zline_pad<E>();
+    static_assert(LPB % 2 == 0 && E % 2 == 0, "pairs of lines");
+    const int pt = threadIdx.x / NT;
+    const int j = threadIdx.x % NT;
+    const int64_t l0 = line0 + 2 * pt;
+    const bool act0 = l0 < a.nlines, act1 = l0 + 1 < a.nlines;
+    LineEx<C, NT, P> ex{(C *)smem + pt * zline_smem_elems<N, E>(), line_bar<NT, PPB>(pt)};
+
+    const R *in0 = (const R *)a.real + (act0 ? l0 : 0) * a.real_pitch;
+    const R *in1 = (const R *)a.real + (act1 ? l0 + 1 : 0) * a.real_pitch;
+    C v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int n = j + i * NT;
+        v[i] = cmake<C>(act0 ? in0[n] : R(0), act1 ? in1[n] : R(0));
+    }
+    line_fft<R, N, E>(v, j, tw, ex);
+
+    constexpr bool LR = pad_linear_reads<P>(NT);
+    constexpr bool LREV = P < 0 || NT % (1 << P) == 0;
+#pragma unroll
+    for (int i = 0; i < E; ++i) ex.put(pad_row<P, LR>(j, i * NT), v[i]);
+    ex.sync();
+    C *out0 = (C *)a.cplx.main + (act0 ? l0 : 0) * (M + 1);
+    C *out1 = out0 + (M + 1);
+    const R he = R(0.5 * a.scale_edge), hm = R(0.5 * a.scale_mid);
+    // slots with k = j + i NT <= M: i < M / NT, and k = M itself for j = 0
+    static_for<0, M / NT + 1>([&](auto II) {
+        constexpr int i = decltype(II)::value;
+        if (i < M / NT || j == 0) {
+            const int k = j + i * NT;
+            const C z = v[i];
+            const C zm = (k == 0 || k == M) ? z : ex.get(pad_row<P, LREV>(N - j, -i * NT));  // Z[N - k]
+            const R f = (k == 0 || k == M) ? he : hm;
+            if (act0) store_out(out0 + k, cmake<C>(f * (z.x + zm.x), f * (z.y - zm.y)));
+            if (act1) store_out(out1 + k, cmake<C>(f * (z.y + zm.y), f * (zm.x - z.x)));
+        }
+    });
+}
+
+// C2R of two lines per complex transform (double, z_paired): thread j
+// builds Z[k] = Xt_l[k] + i Xt_{l+1}[k] for its k = j + i NT from the
+// Hermitian extensions Xt[k] = X[k] (k <= M), conj X[N - k] (k > M) of both
+// stored half spectra (only the real parts of the k = 0 and M entries enter,
+// weighted by scale_edge), reading each entry it needs itself (no exchange),
+// runs the inverse transform, and writes Re z to line l and Im z to line l + 1
+// with the output scale.  CG selects L2-only loads.
+template <typename R, int M, int E, int LPB, bool CG>
+__device__ __forceinline__ void zc2r_pairs(const ZArgs &a, int64_t line0, unsigned char *smem,
+                                           const typename cvec<R>::T *__restrict__ tw)
+{
+    typedef typename cvec<R>::T C;
+    constexpr int N = 2 * M;
+    constexpr int NT = N / E;
+    constexpr int PPB = LPB / 2;
+    constexpr int P = zline_pad<E>();
+    static_assert(LPB % 2 == 0, "pairs of lines");
+    const int pt = threadIdx.x / NT;
+    const int j = threadIdx.x % NT;
+    const int64_t l0 = line0 + 2 * pt;
+    const bool act0 = l0 < a.nlines, act1 = l0 + 1 < a.nlines;
+    LineEx<C, NT, P> ex{(C *)smem + pt * zline_smem_elems<N, E>(), line_bar<NT, PPB>(pt)};
+
+    const C *src0, *src1, *nyq0, *nyq1;
+    const int64_t la = act0 ? l0 : 0, lb = act1 ? l0 + 1 : 0;
+    if (a.cplx.split) {
+        src0 = (const C *)a.cplx.main + la * M;
+        src1 = (const C *)a.cplx.main + lb * M;
+        nyq0 = (const C *)a.cplx.nyq + la;
+        nyq1 = (const C *)a.cplx.nyq + lb;
+    } else {
+        src0 = (const C *)a.cplx.main + la * (M + 1);
+        src1 = (const C *)a.cplx.main + lb * (M + 1);
+        nyq0 = src0 + M;
+        nyq1 = src1 + M;
+    }
+    auto fetch = [&](const C *src, const C *nyq, bool act, int idx) -> C {
+        if (!act) return cmake<C>(R(0), R(0));
+        const C *p = idx == M ? nyq : src + idx;
+        return CG ? load_cg(p) : *p;
+    };
+    const R we = R(a.scale_edge);
+    C v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int k = j + i * NT;
+        const int idx = k <= M ? k : N - k;
+        C x0 = fetch(src0, nyq0, act0, idx), x1 = fetch(src1, nyq1, act1, idx);
+        if (idx == 0 || idx == M) {
+            x0 = cmake<C>(we * x0.x, R(0));
+            x1 = cmake<C>(we * x1.x, R(0));
+        } else if (k > M) {
+            x0 = cconj(x0);
+            x1 = cconj(x1);
+        }
+        // inverse transform as swap(DFT(swap(Z))), Z = x0 + i x1
+        v[i] = cswap(cmake<C>(x0.x - x1.y, x0.y + x1.x));
+    }
+    line_fft<R, N, E>(v, j, tw, ex);
+
+    const R s = R(a.scale_mid);
+    R *out0 = (R *)a.real_out + la * a.real_pitch;
+    R *out1 = (R *)a.real_out + lb * a.real_pitch;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const C z = cswap(v[i]);  // x0 + i x1 at n = j + i NT
+        if (act0) store_out(out0 + j + i * NT, s * z.x);
+        if (act1) store_out(out1 + j + i * NT, s * z.y);
+    }
+}
+
 // One group of LPB lines per block; with LOOP, a grid of a.max_blocks blocks
 // walks the line groups (the host-memory form, bound by the CPU-GPU link).
 // Two instances because the loop slows the one-pass form down (up to 20%
@@ -1325,8 +1455,11 @@ zpass_r2c_kernel(ZArgs a, const typename cvec<R>::T *__restrict__ tw,
     if constexpr (LOOP) {
         for (int64_t blk = blockIdx.x; blk * LPB < a.nlines; blk += gridDim.x) {
             if (blk != blockIdx.x) __syncthreads();  // shared memory free for the next line group
-            zr2c_lines<R, M, E, LPB>(a, blk * LPB, smem_raw, tw, rot);
+            if constexpr (z_paired<R, M>()) zr2c_pairs<R, M, E, LPB>(a, blk * LPB, smem_raw, tw);
+            else zr2c_lines<R, M, E, LPB>(a, blk * LPB, smem_raw, tw, rot);
         }
+    } else if constexpr (z_paired<R, M>()) {
+        zr2c_pairs<R, M, E, LPB>(a, (int64_t)blockIdx.x * LPB, smem_raw, tw);
     } else {
         zr2c_lines<R, M, E, LPB, z_l2pf<R, M, false>()>(a, (int64_t)blockIdx.x * LPB, smem_raw, tw, rot);
     }
@@ -1341,8 +1474,11 @@ zpass_c2r_kernel(ZArgs a, const typename cvec<R>::T *__restrict__ tw,
     if constexpr (LOOP) {
         for (int64_t blk = blockIdx.x; blk * LPB < a.nlines; blk += gridDim.x) {
             if (blk != blockIdx.x) __syncthreads();  // shared memory free for the next line group
-            zc2r_lines<R, M, E, LPB, false>(a, blk * LPB, smem_raw, tw, rot);
+            if constexpr (z_paired<R, M>()) zc2r_pairs<R, M, E, LPB, false>(a, blk * LPB, smem_raw, tw);
+            else zc2r_lines<R, M, E, LPB, false>(a, blk * LPB, smem_raw, tw, rot);
         }
+    } else if constexpr (z_paired<R, M>()) {
+        zc2r_pairs<R, M, E, LPB, false>(a, (int64_t)blockIdx.x * LPB, smem_raw, tw);
     } else {
         zc2r_lines<R, M, E, LPB, false, z_l2pf<R, M, true>()>(a, (int64_t)blockIdx.x * LPB, smem_raw, tw, rot);
     }

@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("shape", [(8, 6, 12), (16, 16, 16), (4, 12, 6), (64, 32, 48), (32, 1024, 8),
-                                   (4, 8, 2048), (4, 8, 1536)],
+                                   (4, 8, 2048), (4, 8, 1536), (3, 3, 1024)],
                          ids=lambda s: "x".join(map(str, s)))
 @pytest.mark.parametrize("name", ["f64", "f32"])
 def test_adjoints_vs_oracle(shape, name):
