@@ -23,7 +23,7 @@ SHAPES = sorted(set(
     + [(4, L, 12) for L in COL_LENGTHS]
     + [(3, 4, 2 * M) for M in Z_HALF]
     + [(1, 1, 2), (2, 2, 2), (1, 4, 8), (4, 1, 8), (16, 16, 16), (24, 48, 96)]
-    + [(3, 1, 1024), (1, 1, 1024), (5, 3, 1024)]  # odd line counts: FP64 lines of 1024 points run in pairs
+    + [(3, 1, 1024), (1, 1, 1024), (3, 3, 1024)]  # odd line counts: FP64 lines of 1024 points run in pairs
 ))
 
 

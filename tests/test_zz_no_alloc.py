@@ -59,7 +59,7 @@ def _run(shape, name, inplace):
 
 
 @pytest.mark.parametrize("shape", [(64, 48, 96), (16, 24, 12), (128, 128, 256), (2048, 8, 16), (4, 2048, 32),
-                                   (1536, 8, 16), (512, 512, 16), (3, 5, 1024)],
+                                   (1536, 8, 16), (512, 512, 16), (3, 3, 1024)],
                          ids=lambda s: "x".join(map(str, s)))
 @pytest.mark.parametrize("name", ["f64", "f32"])
 def test_noalloc_matches_plan_c2r(shape, name):
