@@ -6,6 +6,8 @@
 //               half-spectrum entries X[k] = E[k] + W_N2^k O[k] with
 //               E = (Z[k] + conj Z[M-k]) / 2, O = (Z[k] - conj Z[M-k]) / 2i.
 //               (Step 1 of Sec. 3 along the first of the two plane axes.)
+//               Double lines of N2 = 1024 points instead run two lines per
+//               N2-point complex transform (zr2c_pairs / zc2r_pairs).
 //   zpass_c2r : inverse, contiguous axis 2: the same relation run backwards,
 //               then the M-point inverse FFT, the unpacking into 2M reals and
 //               the 1/(N0 N1 N2) normalisation (the paper's separate
