@@ -191,13 +191,14 @@ def test_c2r_overwrite(shape, name):
     assert rel_l2(out.cpu().numpy(), oracle.irfft3(G, shape)) <= TOL[name]
 
 
-@pytest.mark.parametrize("shape", [(32, 64, 128), (64, 256, 256)], ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("shape", [(32, 64, 128), (64, 256, 256), (16, 256, 1024)], ids=lambda s: "x".join(map(str, s)))
 @pytest.mark.parametrize("name", ["f64", "f32"])
 def test_host_resident_field(name, shape):
     """Forward from, and overwrite-inverse into, pinned host memory (read and
     written directly by the first and last passes, which then run on a
     limited grid of blocks looping over the lines when there are more line
-    groups than that: 512 groups at 64 x 256 x 256).  Same arithmetic as the
+    groups than that: 512 groups at 64 x 256 x 256, and at 16 x 256 x 1024,
+    where FP64 lines run two per complex transform).  Same arithmetic as the
     device-resident calls, so the results must agree bit for bit."""
     import torch
     import paper_2202_12756_gb300 as fft3d
