@@ -419,6 +419,16 @@ def run_reference(args):
     world, rank, local, pg = dist_setup(args)
     if rank != 0:
         return 0
+    if world > 1:
+        # torchrun gives every rank one OpenMP thread; rank 0 runs the oracle alone, on the host's cores.
+        # torch has already started the OpenMP runtime the oracle's library binds to, so set it there.
+        cores = len(os.sched_getaffinity(0))
+        os.environ["OMP_NUM_THREADS"] = str(cores)
+        try:
+            import ctypes
+            ctypes.CDLL("libgomp.so.1").omp_set_num_threads(cores)
+        except (OSError, AttributeError):
+            pass
     import oracle
     import synth
     n = args.ref_n

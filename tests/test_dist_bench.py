@@ -61,3 +61,25 @@ def test_flop_and_byte_models():
     assert bench.pair_flops(1024, 1024, 1024) == pytest.approx(5 * 2 ** 30 * 30)
     # three passes, each reading and writing the array: 25.81 GB per transform in FP32
     assert bench.pass_bytes(1024, 1024, 1024, 4) / 1e9 == pytest.approx(25.81, abs=0.01)
+
+
+def test_reference_arm_under_torchrun():
+    """bench.py --impl reference launched as the two-rank job of a scaling run:
+    rank 0 alone runs the oracle, on the host's cores (torchrun's one OpenMP
+    thread per rank is lifted for it), and prints one line; the other rank
+    exits 0 without work."""
+    import json
+    import subprocess
+    import sys
+    import bench
+    port = _free_port()
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl",
+                        "reference", "--ref-n", "32", "--steps", "1", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=300, cwd=bench.ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.strip().splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2
+    assert line["cpu_baseline"]["cores"] == len(os.sched_getaffinity(0))
